@@ -1,0 +1,337 @@
+"""Benchmark of the fused pseudopotential MRT-LBM step (arXiv:1605.01800) on GB300.
+
+Workload (default): the coexistence-curve batch, 32 independent flat liquid
+slabs of 256x64 periodic nodes at T/Tc = 0.5 .. 0.95, FP32 deviation storage,
+advanced together by one kernel launch per time step. One bench step is one
+time step of the whole batch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: the working set (37.7 MB) fits in the 129 MB L2, so a 256 MiB buffer
+is written before every timed step (outside the timed events) and each step is
+timed alone with CUDA events on the library's stream. The FP64-storage path
+(the plain comparator) is timed the same way. `e2e` times the public C ABI
+with host buffers: upload of every density field, one step, download of every
+density field. `cpu_baseline` times the FP64 CPU oracle on a bounded sample.
+Under torchrun every rank advances its own copy of the batch (weak scaling, no
+collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALG_BYTES_FP32 = 72   # 9 reads + 9 writes of 4 B per node update
+ALG_BYTES_FP64 = 144
+WORKLOAD = "coexistence_batch"
+PROFILE = os.path.join(ROOT, "profiles", "step_fp32_coexistence_batch.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1605_01800_gb300", "csrc", f)
+                  for f in ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="time budget of the oracle sample for cpu_baseline")
+    return ap.parse_args()
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def time_oracle(specs, seconds, min_steps=1):
+    """FP64 oracle over the whole batch, whole time steps until `seconds` pass."""
+    from oracle import d2q9
+    lats = []
+    for s in specs:
+        L = d2q9.Lattice(s.nx, s.ny, a=s.a, b=s.b, R=s.R, T=s.T, G=s.G, s=s.s, eps=s.eps, solid=s.solid)
+        L.init(s.rho)
+        lats.append(L)
+    nodes = sum(s.nodes for s in specs)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        for L in lats:
+            L.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= min_steps and el >= seconds:
+            break
+    return nodes * steps / el / 1e6, steps, el
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from paper_1605_01800_gb300 import inputs
+    specs = inputs.coexistence_batch()
+    nodes = sum(s.nodes for s in specs)
+    from oracle import d2q9
+    lats = []
+    for s in specs:
+        L = d2q9.Lattice(s.nx, s.ny, a=s.a, b=s.b, R=s.R, T=s.T, G=s.G, s=s.s, eps=s.eps, solid=s.solid)
+        L.init(s.rho)
+        lats.append(L)
+    for _ in range(args.warmup):
+        for L in lats:
+            L.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for L in lats:
+            L.step(1)
+    el = time.perf_counter() - t0
+    mlups = nodes * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattices": len(specs), "nx": 256, "ny": 64,
+                   "nodes_per_step": nodes, "precision": "fp64 CPU oracle"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} whole time steps of all {len(specs)} lattices"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(torch, ctx, lbm, stream, flush, steps):
+    """Per-step CUDA-event times (ms) of lbm_step(ctx, 1), L2 flushed before each."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            lbm.lbm_step(ctx, 1)
+            e1.record(stream)
+    stream.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_1605_01800_gb300 import inputs, lbm
+    lbm.load()
+    specs = inputs.coexistence_batch()
+    nodes = sum(s.nodes for s in specs)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- FP32 deviation storage (the product path)
+    b32 = lbm.Batch(specs, "fp32_dev", stream=stream)
+    b32.init()
+    timed_steps(torch, b32.ctx, lbm, stream, flush, max(args.warmup, 3))
+    launches0 = b32.info()["kernel_launches"]
+    clocks = ClockSampler(dev)
+    barrier()
+    t_wall0 = time.perf_counter()
+    ms = timed_steps(torch, b32.ctx, lbm, stream, flush, args.steps)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = b32.info()["kernel_launches"] - launches0
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    mlups = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
+    lbm.lbm_sync(b32.ctx)
+
+    # steady state with the working set resident in L2 (no flush), for context
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lbm.lbm_step(b32.ctx, 64)
+        e0.record(stream)
+        lbm.lbm_step(b32.ctx, 256)
+        e1.record(stream)
+    stream.synchronize()
+    l2_mlups = nodes * 256 / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    # ---- e2e through the C ABI with host buffers
+    rho_in = torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
+    rho_in[:] = np.concatenate([s.rho.ravel() for s in specs])
+    rho_out = torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        lbm.lbm_init_fields_all(b32.ctx, rho_in)
+        lbm.lbm_step(b32.ctx, 1)
+        lbm.lbm_read_moments_all(b32.ctx, rho_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lbm.lbm_init_fields_all(b32.ctx, rho_in)
+        lbm.lbm_step(b32.ctx, 1)
+        lbm.lbm_read_moments_all(b32.ctx, rho_out)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_mlups = world * nodes * e2e_steps / e2e_s / 1e6
+    b32.close()
+
+    # ---- FP64 plain storage (the comparator)
+    b64 = lbm.Batch(specs, "fp64", stream=stream)
+    b64.init()
+    timed_steps(torch, b64.ctx, lbm, stream, flush, 3)
+    k64 = max(3, min(args.steps, 50))
+    ms64 = timed_steps(torch, b64.ctx, lbm, stream, flush, k64)
+    fp64_ms = sum(ms64) / k64
+    fp64_mlups = nodes / (fp64_ms * 1e-3) / 1e6
+    b64.close()
+
+    peak, peak_kind = measured_peak_hbm()
+    achieved = ALG_BYTES_FP32 * nodes / (ms_per_step * 1e-3) / 1e9
+    traffic = profiled_traffic()
+
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattices": len(specs), "nx": 256, "ny": 64,
+                   "nodes_per_step_per_gpu": nodes, "precision": "fp32 deviation storage",
+                   "tile": lbm.lbm_tile_shape(0), "l2": "256 MiB buffer written before every timed step",
+                   "parallelism": f"{world} independent batch replica(s), no collective"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_node": ALG_BYTES_FP32},
+        "fp64_plain": {"value": fp64_mlups, "unit": "MLUPS", "ms_per_step": fp64_ms, "steps": k64,
+                       "achieved_gbs": ALG_BYTES_FP64 * nodes / (fp64_ms * 1e-3) / 1e9},
+        "l2_resident": {"value": l2_mlups, "unit": "MLUPS",
+                        "note": "256 back-to-back steps in CUDA graphs without flushing L2"},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "steps": e2e_steps,
+                "h2d_bytes_per_step": nodes * 8, "d2h_bytes_per_step": nodes * 8,
+                "path": "lbm_init_fields_all(host rho) + lbm_step(1) + lbm_read_moments_all(host rho)"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed_loop": t_wall,
+    }
+    if rank == 0 and world == 1:
+        cpu_mlups, cpu_steps, cpu_s = time_oracle(specs, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": cpu_mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"{cpu_steps} whole time steps of all {len(specs)} lattices "
+                                          f"({cpu_s:.1f} s, single thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * lbm.h - C ABI of the GB300 pseudopotential MRT lattice Boltzmann library.
+ *
+ * The library advances batches of independent two-dimensional D2Q9 lattices
+ * with the scheme of Shan et al., "Pseudopotential MRT lattice Boltzmann
+ * model for cavitation bubble collapse with high density ratio"
+ * (arXiv:1605.01800):
+ *   - MRT collision in moment space, Eq. 1-4, relaxation rates Lambda of Eq. 2;
+ *   - the pseudopotential interaction force of Eq. 7 with psi of Eq. 13 and
+ *     the Carnahan-Starling EOS of Eq. 15;
+ *   - Li's modified forcing source of Eq. 14 (epsilon), velocity of Eq. 6;
+ *   - streaming, Eq. 5, periodic in x and y, with no-slip halfway bounce-back
+ *     at solid nodes (Sec. 4.1).
+ * Lattice units: delta_x = delta_t = c = 1, c_s^2 = 1/3.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns LBM_OK (0) or an LBM_E* code; lbm_last_error()
+ *     then holds a message for the calling thread.
+ *   - Host arrays of one lattice are row-major nx*ny doubles (x fastest). The
+ *     "_all" variants take the lattices of a batch concatenated in creation
+ *     order (sum of nx*ny doubles).
+ *   - Host pointers may be pageable or pinned; the library copies them
+ *     (inputs) or fills them (outputs) and never keeps them.
+ *   - Device memory is owned by the context and released by lbm_destroy().
+ *   - Work is enqueued on the context's stream (lbm_set_stream). Entry points
+ *     that return data to the host synchronise that stream.
+ *   - Device-side errors (psi^2 < 0 clamped, a non-finite density) are sticky
+ *     per lattice; they are reported by lbm_status() and turn the return code
+ *     of lbm_read_moments*, lbm_total_mass and lbm_sync into
+ *     LBM_EPSI_DOMAIN or LBM_ENONFINITE (the data is still written).
+ *   - A context is not thread-safe; distinct contexts may be used from
+ *     distinct threads.
+ */
+#ifndef PAPER_1605_01800_GB300_LBM_H
+#define PAPER_1605_01800_GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_EINVAL 1          /* invalid argument (message says which) */
+#define LBM_ENOMEM 2          /* device or host allocation failed */
+#define LBM_ECUDA 3           /* a CUDA runtime call failed */
+#define LBM_EPSI_DOMAIN 4     /* psi^2 of Eq. 13 went negative somewhere and was clamped to 0 */
+#define LBM_ENONFINITE 5      /* a density or psi^2 became NaN or infinite */
+
+/* ---- storage precision (lbm_create*, argument `precision`) --------------- */
+#define LBM_FP32_DEV 0        /* FP32 storage and collision of f_a - w_a rho_ref */
+#define LBM_FP32 1            /* FP32 storage of f_a (rho_ref forced to 0) */
+#define LBM_FP64 2            /* FP64 storage and arithmetic */
+
+/* ---- sticky per-lattice status bits (lbm_status) ------------------------- */
+#define LBM_FLAG_PSI_CLAMPED 1u
+#define LBM_FLAG_NONFINITE 2u
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Carnahan-Starling EOS of Eq. 15, p = rho R T (1 + h + h^2 - h^3)/(1 - h)^3
+ * - a rho^2 with h = b rho / 4, and the interaction strength G of Eq. 7 and
+ * Eq. 13 (G < 0; the paper uses G = -1). */
+typedef struct {
+    double a, b, R, T, G;
+} lbm_eos_params;
+
+/* One lattice of a batch.
+ *   nx, ny     lattice size, each >= 1; 9 * ny * round_up(nx, 32) < 2^31.
+ *   eos        Eq. 15 and G.
+ *   s          diagonal of Lambda (Eq. 2) in the moment order
+ *              (rho, e, zeta, j_x, q_x, j_y, q_y, p_xx, p_xy); each in [0, 2).
+ *   eps        epsilon of Li's term, Eq. 14.
+ *   rho_ref    FP32_DEV only: the reference density of the stored deviation
+ *              f_a - w_a rho_ref. > 0: used as given; 0: plain FP32 storage;
+ *              < 0: taken as the maximum of the first density field passed to
+ *              lbm_init_fields*. Ignored for LBM_FP32 and LBM_FP64.
+ *   wall_mask  NULL (no solid nodes) or nx*ny bytes, nonzero = solid node. It
+ *              is copied. Solid nodes are not updated; a fluid node's link
+ *              that would stream into a solid node is reflected (halfway
+ *              bounce-back), and a solid neighbour in the force sum of Eq. 7
+ *              takes the psi of the fluid node being updated. */
+typedef struct {
+    int nx, ny;
+    lbm_eos_params eos;
+    double s[9];
+    double eps;
+    double rho_ref;
+    const uint8_t* wall_mask;
+} lbm_lattice_desc;
+
+/* Context introspection (lbm_info). */
+typedef struct {
+    int n_lattices;
+    int precision;
+    long long nodes;           /* sum of nx*ny */
+    long long fluid_nodes;     /* nodes that are not solid */
+    long long steps;           /* time steps taken since the last init/load */
+    unsigned long long kernel_launches; /* kernels this context has launched */
+    size_t device_bytes;       /* device memory held by the context */
+    int tile_x, tile_y;        /* node tile of one CTA of the step kernel */
+    int n_tiles;               /* CTAs of one step launch */
+    int graph_chunk;           /* steps per CUDA-graph replay in lbm_step */
+} lbm_info_t;
+
+/* Create a one-lattice context (the paper's single-domain runs, Sec. 3-4).
+ * eps is the epsilon of Eq. 14; relax_rates the nine rates of Eq. 2. For
+ * LBM_FP32_DEV the deviation reference is the maximum of the first density
+ * field given to lbm_init_fields. The context starts in the rest state
+ * rho = 0 until lbm_init_fields is called. */
+int lbm_create(int nx, int ny, const lbm_eos_params* eos, const double relax_rates[9],
+               double eps, const uint8_t* wall_mask, int precision, lbm_ctx** out);
+
+/* Create a context advancing n independent lattices of any sizes together:
+ * each lbm_step advances every lattice by one time step in one launch. */
+int lbm_create_batch(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** out);
+
+/* Run the context's work on `cuda_stream` (a cudaStream_t, e.g. PyTorch's
+ * torch.cuda.Stream().cuda_stream); NULL selects the legacy default stream,
+ * on which lbm_step launches kernels one by one instead of replaying a graph. */
+int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Set lattice `lat` to the equilibrium f_eq(rho, u) of Eq. 4 at every fluid
+ * node (host arrays, nx*ny doubles; ux/uy may be NULL for u = 0) and reset the
+ * step counter. The state is then the distribution at time 0 (before the
+ * first collision). Densities must be > 0 and finite at fluid nodes. */
+int lbm_init_fields(lbm_ctx* ctx, int lat, const double* rho, const double* ux, const double* uy);
+
+/* lbm_init_fields for every lattice, inputs concatenated in creation order. */
+int lbm_init_fields_all(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+
+/* Advance every lattice by n >= 0 time steps (Eq. 1: collision, Eq. 3, then
+ * streaming, Eq. 5). Asynchronous on the context's stream. With a non-default
+ * stream, whole chunks of `graph_chunk` steps replay a captured CUDA graph. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of lattice `lat` at the current time: rho = sum_a f_a,
+ * v of Eq. 6 (with the force of Eq. 7), p of Eq. 10. Host outputs of nx*ny
+ * doubles; any may be NULL. Solid nodes read as 0. Synchronises the stream. */
+int lbm_read_moments(lbm_ctx* ctx, int lat, double* rho, double* ux, double* uy, double* p);
+
+/* lbm_read_moments for every lattice, outputs concatenated in creation order. */
+int lbm_read_moments_all(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* p);
+
+/* Total mass sum_x rho(x) over the fluid nodes of lattice `lat`, reduced in
+ * FP64 in a fixed order (bitwise reproducible). Synchronises the stream. */
+int lbm_total_mass(lbm_ctx* ctx, int lat, double* mass);
+
+/* Sticky status bits LBM_FLAG_* of lattice `lat` (0 if clean). Synchronises. */
+int lbm_status(lbm_ctx* ctx, int lat, uint32_t* flags);
+
+/* Clear the sticky status bits of every lattice. */
+int lbm_clear_status(lbm_ctx* ctx);
+
+/* Wait for the context's stream; returns a sticky device error if any. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Checkpoint: size in bytes of the state blob, and save/load of the raw
+ * distributions plus the step counter. A blob loads only into a context
+ * created with the same lattices and precision. */
+int lbm_state_size(lbm_ctx* ctx, size_t* bytes);
+int lbm_save_state(lbm_ctx* ctx, void* buf, size_t bytes);
+int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Select the CTA tile of the step kernel by index into the built-in list
+ * (lbm_tile_count() entries; lbm_tile_shape gives each shape). Results are
+ * bitwise identical for every tile. */
+int lbm_tile_count(void);
+int lbm_tile_shape(int index, int* tile_x, int* tile_y);
+int lbm_set_tile(lbm_ctx* ctx, int index);
+
+/* Time every built-in tile on this context's lattices for `steps` steps each
+ * (CUDA events on the context's stream), keep the fastest and report its
+ * index and the per-step milliseconds of each candidate (ms may be NULL,
+ * else lbm_tile_count() doubles). The state is saved before and restored
+ * after, so the simulation is unchanged. */
+int lbm_autotune(lbm_ctx* ctx, int steps, int* best_index, double* ms);
+
+/* Context introspection. */
+int lbm_info(lbm_ctx* ctx, lbm_info_t* info);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* Release the context and its device memory (NULL is ignored). */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_1605_01800_GB300_LBM_H */

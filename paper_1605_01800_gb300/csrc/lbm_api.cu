@@ -1,0 +1,796 @@
+// Runtime and C ABI of the library (declared in include/lbm.h): context,
+// parameter validation, device buffers, batch work-list, CUDA-graph replay of
+// time steps, tile autotuning, read-out and checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.h"
+#include "lbm_step.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr double kCs2 = 1.0 / 3.0;
+constexpr double kWeq[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                            1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+constexpr int kGraphChunk = 32;  // steps per captured graph (even: parity is preserved)
+constexpr uint32_t kStateMagic = 0x4c424d31u;  // "LBM1"
+
+struct HostLattice {
+    lbm_lattice_desc desc;       // wall_mask pointer not kept
+    std::vector<uint8_t> mask;   // nx*ny, empty if none
+    Geom geom;
+    double rho_ref;              // as used by the kernels (FP32-rounded for FP32_DEV)
+    bool rho_ref_auto;
+    long long n_fluid;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    int n = 0;
+    int precision = LBM_FP32_DEV;
+    size_t elem = 4;
+    std::vector<HostLattice> lats;
+    long long total_nodes = 0, fluid_nodes = 0;
+    long long total_elems = 0;   // elements per distribution array
+    long long mask_bytes = 0;
+    long long max_nodes = 0;
+
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;                 // buffer holding the state read by the next step
+    uint8_t* d_mask = nullptr;
+    Geom* d_geom = nullptr;
+    Phys<float>* d_phys_f = nullptr;
+    Phys<double>* d_phys_d = nullptr;
+    Tile* d_tiles = nullptr;
+    int n_tiles = 0;
+    int tile_index = 0;
+    unsigned* d_status = nullptr;
+    double* d_partials = nullptr;
+    double* d_scalar = nullptr;
+    double* d_io = nullptr;      // staging: 4 * max_nodes doubles
+    std::vector<Phys<double>> phys_d;
+    size_t device_bytes = 0;
+
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk graphs by starting buffer
+    long long steps = 0;
+    unsigned long long launches = 0;
+};
+
+namespace {
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+int validate_desc(const lbm_lattice_desc& d, int i) {
+    if (d.nx < 1 || d.ny < 1) return fail(LBM_EINVAL, "lattice %d: nx=%d, ny=%d must be >= 1", i, d.nx, d.ny);
+    long long plane = (long long)d.ny * round_up(d.nx, 32);
+    if (9 * plane >= (1ll << 31))
+        return fail(LBM_EINVAL, "lattice %d: %dx%d too large (9*ny*pitch must be < 2^31)", i, d.nx, d.ny);
+    const lbm_eos_params& e = d.eos;
+    if (!(std::isfinite(e.a) && std::isfinite(e.b) && std::isfinite(e.R) && std::isfinite(e.T) &&
+          std::isfinite(e.G)))
+        return fail(LBM_EINVAL, "lattice %d: EOS parameters must be finite", i);
+    if (!(e.b > 0.0)) return fail(LBM_EINVAL, "lattice %d: b must be > 0 (Eq. 15)", i);
+    if (!(e.G < 0.0)) return fail(LBM_EINVAL, "lattice %d: G must be < 0 for psi of Eq. 13", i);
+    if (!(e.R * e.T >= 0.0)) return fail(LBM_EINVAL, "lattice %d: R*T must be >= 0", i);
+    for (int k = 0; k < 9; ++k)
+        if (!(d.s[k] >= 0.0 && d.s[k] < 2.0))
+            return fail(LBM_EINVAL, "lattice %d: relaxation rate s[%d]=%g outside [0, 2)", i, k, d.s[k]);
+    if (!std::isfinite(d.eps)) return fail(LBM_EINVAL, "lattice %d: eps must be finite", i);
+    if (!std::isfinite(d.rho_ref)) return fail(LBM_EINVAL, "lattice %d: rho_ref must be finite", i);
+    return LBM_OK;
+}
+
+void fill_phys(const HostLattice& L, Phys<double>& P) {
+    const lbm_lattice_desc& d = L.desc;
+    P.rho_ref = L.rho_ref;
+    P.RT = d.eos.R * d.eos.T;
+    P.a = d.eos.a;
+    P.b4 = d.eos.b / 4.0;
+    P.G = d.eos.G;
+    P.kpsi = 2.0 / d.eos.G;  // c = 1
+    P.cs2 = kCs2;
+    for (int k = 0; k < 9; ++k) P.s[k] = d.s[k];
+    P.li_e = d.s[1] * 0.75 * d.eps;
+    P.li_z = d.s[2] * 0.75 * d.eps;
+}
+
+void to_float(const Phys<double>& D, Phys<float>& F) {
+    F.rho_ref = (float)D.rho_ref;
+    F.RT = (float)D.RT;
+    F.a = (float)D.a;
+    F.b4 = (float)D.b4;
+    F.G = (float)D.G;
+    F.kpsi = (float)D.kpsi;
+    F.cs2 = (float)D.cs2;
+    for (int k = 0; k < 9; ++k) F.s[k] = (float)D.s[k];
+    F.li_e = (float)D.li_e;
+    F.li_z = (float)D.li_z;
+}
+
+template <typename P>
+int dev_alloc(lbm_ctx* c, P** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->device_bytes += bytes;
+    return LBM_OK;
+}
+
+void drop_graphs(lbm_ctx* c) {
+    for (auto& g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+void free_ctx(lbm_ctx* c) {
+    if (!c) return;
+    drop_graphs(c);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->d_mask);
+    cudaFree(c->d_geom);
+    cudaFree(c->d_phys_f);
+    cudaFree(c->d_phys_d);
+    cudaFree(c->d_tiles);
+    cudaFree(c->d_status);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_scalar);
+    cudaFree(c->d_io);
+    delete c;
+}
+
+// Work-list of one step launch: every tile of every lattice, lattices in
+// creation order, tiles row-major within a lattice.
+int build_tiles(lbm_ctx* c, int tile_index) {
+    const int tx = kTiles[tile_index][0], ty = kTiles[tile_index][1];
+    std::vector<Tile> tiles;
+    for (int l = 0; l < c->n; ++l) {
+        const Geom& g = c->lats[l].geom;
+        for (int y0 = 0; y0 < g.ny; y0 += ty)
+            for (int x0 = 0; x0 < g.nx; x0 += tx) tiles.push_back(Tile{l, x0, y0, 0});
+    }
+    if (tiles.size() > (size_t)0x7fffffff) return fail(LBM_EINVAL, "too many tiles");
+    Tile* d = nullptr;
+    int rc = dev_alloc(c, &d, tiles.size() * sizeof(Tile));
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(tiles)");
+    }
+    if (c->d_tiles) {
+        cudaFree(c->d_tiles);
+        c->device_bytes -= (size_t)c->n_tiles * sizeof(Tile);
+    }
+    c->d_tiles = d;
+    c->n_tiles = (int)tiles.size();
+    c->tile_index = tile_index;
+    drop_graphs(c);
+    return LBM_OK;
+}
+
+int upload_phys(lbm_ctx* c) {
+    std::vector<Phys<float>> pf(c->n);
+    for (int l = 0; l < c->n; ++l) {
+        fill_phys(c->lats[l], c->phys_d[l]);
+        to_float(c->phys_d[l], pf[l]);
+    }
+    CK(cudaMemcpy(c->d_phys_d, c->phys_d.data(), c->n * sizeof(Phys<double>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_phys_f, pf.data(), c->n * sizeof(Phys<float>), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+// One step launch from buffer `src` into buffer 1 - src.
+cudaError_t launch_one_step(lbm_ctx* c, int src) {
+    if (c->precision == LBM_FP64) {
+        StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
+                           (double*)c->f[1 - src], c->d_mask, c->d_status};
+        return launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
+    }
+    StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
+                      (float*)c->f[1 - src], c->d_mask, c->d_status};
+    return launch_step_f32(c->tile_index, c->n_tiles, a, c->stream);
+}
+
+bool capturable_stream(cudaStream_t s) {
+    return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
+int ensure_graph(lbm_ctx* c, int src) {
+    if (c->graph[src]) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kGraphChunk && le == cudaSuccess; ++k) le = launch_one_step(c, (src + k) & 1);
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "step launch during graph capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&c->graph[src], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->graph[src] = nullptr;
+        return cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    return LBM_OK;
+}
+
+int check_lat(lbm_ctx* c, int lat) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (lat < 0 || lat >= c->n) return fail(LBM_EINVAL, "lattice index %d outside [0, %d)", lat, c->n);
+    return LBM_OK;
+}
+
+int status_code(unsigned flags) {
+    if (flags & FLAG_NONFINITE) return fail(LBM_ENONFINITE, "a density or psi^2 became non-finite");
+    if (flags & FLAG_PSI_CLAMPED)
+        return fail(LBM_EPSI_DOMAIN, "psi^2 of Eq. 13 went negative and was clamped to 0");
+    return LBM_OK;
+}
+
+int read_status(lbm_ctx* c, std::vector<unsigned>& out) {
+    out.assign(c->n, 0u);
+    CK(cudaMemcpyAsync(out.data(), c->d_status, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int init_one(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy) {
+    HostLattice& L = c->lats[lat];
+    const Geom& g = L.geom;
+    const long long n = (long long)g.nx * g.ny;
+    const uint8_t* m = L.mask.empty() ? nullptr : L.mask.data();
+    double rmax = 0.0;
+    for (long long i = 0; i < n; ++i) {
+        if (m && m[i]) continue;
+        if (!(std::isfinite(rho[i]) && rho[i] > 0.0))
+            return fail(LBM_EINVAL, "lattice %d: rho[%lld]=%g must be finite and > 0", lat, i, rho[i]);
+        if ((ux && !std::isfinite(ux[i])) || (uy && !std::isfinite(uy[i])))
+            return fail(LBM_EINVAL, "lattice %d: velocity at %lld is not finite", lat, i);
+        rmax = std::max(rmax, rho[i]);
+    }
+    if (c->precision == LBM_FP32_DEV && L.rho_ref_auto) {
+        L.rho_ref = (double)(float)rmax;
+        L.rho_ref_auto = false;
+        int rc = upload_phys(c);
+        if (rc) return rc;
+        drop_graphs(c);
+    }
+    double* d_rho = c->d_io;
+    double* d_ux = ux ? c->d_io + c->max_nodes : nullptr;
+    double* d_uy = uy ? c->d_io + 2 * c->max_nodes : nullptr;
+    CK(cudaMemcpyAsync(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (ux) CK(cudaMemcpyAsync(d_ux, ux, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (uy) CK(cudaMemcpyAsync(d_uy, uy, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const uint8_t* dm = L.mask.empty() ? nullptr : c->d_mask + g.mask_off;
+    cudaError_t e;
+    if (c->precision == LBM_FP64)
+        e = launch_init_f64(g, L.rho_ref, d_rho, d_ux, d_uy, dm, (double*)c->f[c->cur], c->stream);
+    else
+        e = launch_init_f32(g, (float)L.rho_ref, d_rho, d_ux, d_uy, dm, (float*)c->f[c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    c->launches += 1;
+    // the staging buffer is reused by the next call: wait for the copies
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int moments_one(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, double* p) {
+    const HostLattice& L = c->lats[lat];
+    const Geom& g = L.geom;
+    const long long n = (long long)g.nx * g.ny;
+    double* d[4] = {rho ? c->d_io : nullptr, ux ? c->d_io + c->max_nodes : nullptr,
+                    uy ? c->d_io + 2 * c->max_nodes : nullptr, p ? c->d_io + 3 * c->max_nodes : nullptr};
+    const uint8_t* dm = L.mask.empty() ? nullptr : c->d_mask + g.mask_off;
+    cudaError_t e;
+    if (c->precision == LBM_FP64)
+        e = launch_moments_f64(g, c->phys_d[lat], (const double*)c->f[c->cur], dm, d[0], d[1], d[2], d[3], c->stream);
+    else
+        e = launch_moments_f32(g, c->phys_d[lat], (const float*)c->f[c->cur], dm, d[0], d[1], d[2], d[3], c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
+    c->launches += 1;
+    double* h[4] = {rho, ux, uy, p};
+    for (int k = 0; k < 4; ++k)
+        if (h[k]) CK(cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** out) {
+    if (!out) return fail(LBM_EINVAL, "out is null");
+    *out = nullptr;
+    if (n < 1 || !desc) return fail(LBM_EINVAL, "need n >= 1 lattice descriptions");
+    if (precision != LBM_FP32_DEV && precision != LBM_FP32 && precision != LBM_FP64)
+        return fail(LBM_EINVAL, "unknown precision %d", precision);
+    for (int i = 0; i < n; ++i) {
+        int rc = validate_desc(desc[i], i);
+        if (rc) return rc;
+    }
+    int dev_count = 0;
+    cudaError_t de = cudaGetDeviceCount(&dev_count);
+    if (de != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "no CUDA device available: %s", cudaGetErrorString(de));
+    }
+
+    lbm_ctx* c = new lbm_ctx();
+    c->n = n;
+    c->precision = precision;
+    c->elem = precision == LBM_FP64 ? 8 : 4;
+    c->lats.resize(n);
+    c->phys_d.resize(n);
+    long long f_off = 0, m_off = 0, node_off = 0;
+    for (int i = 0; i < n; ++i) {
+        HostLattice& L = c->lats[i];
+        L.desc = desc[i];
+        L.desc.wall_mask = nullptr;
+        Geom& g = L.geom;
+        g.nx = desc[i].nx;
+        g.ny = desc[i].ny;
+        g.pitch = (int)round_up(g.nx, 32);
+        g.plane = (long long)g.ny * g.pitch;
+        g.f_off = f_off;
+        g.node_off = node_off;
+        const long long nn = (long long)g.nx * g.ny;
+        L.n_fluid = nn;
+        if (desc[i].wall_mask) {
+            L.mask.assign(desc[i].wall_mask, desc[i].wall_mask + nn);
+            for (auto& b : L.mask) b = b ? 1 : 0;
+            L.n_fluid = 0;
+            for (auto b : L.mask) L.n_fluid += (b == 0);
+            g.has_mask = 1;
+            g.mask_off = m_off;
+            m_off += round_up(g.plane, 256);
+        } else {
+            g.has_mask = 0;
+            g.mask_off = 0;
+        }
+        // keep each lattice's planes 256-byte aligned
+        f_off += round_up(9 * g.plane, 64);
+        node_off += nn;
+        c->total_nodes += nn;
+        c->fluid_nodes += L.n_fluid;
+        c->max_nodes = std::max(c->max_nodes, nn);
+        if (precision == LBM_FP32_DEV) {
+            L.rho_ref_auto = desc[i].rho_ref < 0.0;
+            L.rho_ref = L.rho_ref_auto ? 0.0 : (double)(float)desc[i].rho_ref;
+        } else {
+            L.rho_ref_auto = false;
+            L.rho_ref = 0.0;
+        }
+    }
+    c->total_elems = f_off;
+    c->mask_bytes = m_off;
+
+    int rc = LBM_OK;
+    const size_t fbytes = (size_t)c->total_elems * c->elem;
+    if (!rc) rc = dev_alloc(c, &c->f[0], fbytes);
+    if (!rc) rc = dev_alloc(c, &c->f[1], fbytes);
+    if (!rc && m_off > 0) rc = dev_alloc(c, &c->d_mask, (size_t)m_off);
+    if (!rc) rc = dev_alloc(c, &c->d_geom, n * sizeof(Geom));
+    if (!rc) rc = dev_alloc(c, &c->d_phys_f, n * sizeof(Phys<float>));
+    if (!rc) rc = dev_alloc(c, &c->d_phys_d, n * sizeof(Phys<double>));
+    if (!rc) rc = dev_alloc(c, &c->d_status, n * sizeof(unsigned));
+    if (!rc) rc = dev_alloc(c, &c->d_partials, kMassBlocks * sizeof(double));
+    if (!rc) rc = dev_alloc(c, &c->d_scalar, sizeof(double));
+    if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->max_nodes * sizeof(double));
+    if (rc) {
+        free_ctx(c);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemset(c->f[0], 0, fbytes);
+    if (e == cudaSuccess) e = cudaMemset(c->f[1], 0, fbytes);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, n * sizeof(unsigned));
+    if (e == cudaSuccess && m_off > 0) {
+        e = cudaMemset(c->d_mask, 0, (size_t)m_off);
+        std::vector<uint8_t> rows;
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            const HostLattice& L = c->lats[i];
+            if (L.mask.empty()) continue;
+            const Geom& g = L.geom;
+            rows.assign((size_t)g.plane, 0);
+            for (int y = 0; y < g.ny; ++y)
+                memcpy(&rows[(size_t)y * g.pitch], &L.mask[(size_t)y * g.nx], g.nx);
+            e = cudaMemcpy(c->d_mask + g.mask_off, rows.data(), rows.size(), cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) {
+        std::vector<Geom> geoms(n);
+        for (int i = 0; i < n; ++i) geoms[i] = c->lats[i].geom;
+        e = cudaMemcpy(c->d_geom, geoms.data(), n * sizeof(Geom), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "context set-up copy");
+        free_ctx(c);
+        return rc;
+    }
+    rc = upload_phys(c);
+    if (!rc) rc = build_tiles(c, 0);
+    if (rc) {
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(int nx, int ny, const lbm_eos_params* eos, const double relax_rates[9], double eps,
+               const uint8_t* wall_mask, int precision, lbm_ctx** out) {
+    g_last_error.clear();
+    if (!eos || !relax_rates) return fail(LBM_EINVAL, "eos and relax_rates must not be null");
+    lbm_lattice_desc d;
+    d.nx = nx;
+    d.ny = ny;
+    d.eos = *eos;
+    for (int k = 0; k < 9; ++k) d.s[k] = relax_rates[k];
+    d.eps = eps;
+    d.rho_ref = -1.0;  // FP32_DEV: maximum of the first density field
+    d.wall_mask = wall_mask;
+    return create_common(1, &d, precision, out);
+}
+
+int lbm_create_batch(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** out) {
+    g_last_error.clear();
+    return create_common(n, desc, precision, out);
+}
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s != c->stream) {
+        drop_graphs(c);
+        c->stream = s;
+    }
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy) {
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    if (!rho) return fail(LBM_EINVAL, "rho must not be null");
+    rc = init_one(c, lat, rho, ux, uy);
+    if (rc) return rc;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_init_fields_all(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (!rho) return fail(LBM_EINVAL, "rho must not be null");
+    for (int l = 0; l < c->n; ++l) {
+        const long long o = c->lats[l].geom.node_off;
+        int rc = init_one(c, l, rho + o, ux ? ux + o : nullptr, uy ? uy + o : nullptr);
+        if (rc) return rc;
+    }
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (n < 0) return fail(LBM_EINVAL, "n=%d must be >= 0", n);
+    int done = 0;
+    if (capturable_stream(c->stream)) {
+        while (n - done >= kGraphChunk) {
+            int rc = ensure_graph(c, c->cur);
+            if (rc) return rc;
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            c->launches += kGraphChunk;
+            done += kGraphChunk;
+            c->steps += kGraphChunk;  // kGraphChunk is even: c->cur unchanged
+        }
+    }
+    for (; done < n; ++done) {
+        cudaError_t e = launch_one_step(c, c->cur);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        c->launches += 1;
+        c->cur ^= 1;
+        c->steps += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_read_moments(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, double* p) {
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    rc = moments_one(c, lat, rho, ux, uy, p);
+    if (rc) return rc;
+    std::vector<unsigned> st;
+    rc = read_status(c, st);
+    if (rc) return rc;
+    return status_code(st[lat]);
+}
+
+int lbm_read_moments_all(lbm_ctx* c, double* rho, double* ux, double* uy, double* p) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    for (int l = 0; l < c->n; ++l) {
+        const long long o = c->lats[l].geom.node_off;
+        int rc = moments_one(c, l, rho ? rho + o : nullptr, ux ? ux + o : nullptr,
+                             uy ? uy + o : nullptr, p ? p + o : nullptr);
+        if (rc) return rc;
+    }
+    std::vector<unsigned> st;
+    int rc = read_status(c, st);
+    if (rc) return rc;
+    unsigned all = 0;
+    for (unsigned s : st) all |= s;
+    return status_code(all);
+}
+
+int lbm_total_mass(lbm_ctx* c, int lat, double* mass) {
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    if (!mass) return fail(LBM_EINVAL, "mass must not be null");
+    const HostLattice& L = c->lats[lat];
+    const uint8_t* dm = L.mask.empty() ? nullptr : c->d_mask + L.geom.mask_off;
+    cudaError_t e;
+    if (c->precision == LBM_FP64)
+        e = launch_mass_f64(L.geom, L.rho_ref, L.n_fluid, (const double*)c->f[c->cur], dm, c->d_partials,
+                            c->d_scalar, c->stream);
+    else
+        e = launch_mass_f32(L.geom, L.rho_ref, L.n_fluid, (const float*)c->f[c->cur], dm, c->d_partials,
+                            c->d_scalar, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mass kernels");
+    c->launches += 2;
+    CK(cudaMemcpyAsync(mass, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<unsigned> st;
+    rc = read_status(c, st);
+    if (rc) return rc;
+    return status_code(st[lat]);
+}
+
+int lbm_status(lbm_ctx* c, int lat, uint32_t* flags) {
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    if (!flags) return fail(LBM_EINVAL, "flags must not be null");
+    std::vector<unsigned> st;
+    rc = read_status(c, st);
+    if (rc) return rc;
+    *flags = st[lat];
+    return LBM_OK;
+}
+
+int lbm_clear_status(lbm_ctx* c) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    CK(cudaMemsetAsync(c->d_status, 0, c->n * sizeof(unsigned), c->stream));
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    std::vector<unsigned> st;
+    int rc = read_status(c, st);
+    if (rc) return rc;
+    unsigned all = 0;
+    for (unsigned s : st) all |= s;
+    return status_code(all);
+}
+
+int lbm_state_size(lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(LBM_EINVAL, "null argument");
+    *bytes = 4 * sizeof(uint32_t) + sizeof(long long) + c->n * sizeof(double) +
+             (size_t)c->total_elems * c->elem;
+    return LBM_OK;
+}
+
+int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lbm_state_size(c, &need);
+    if (rc) return rc;
+    if (!buf || bytes < need) return fail(LBM_EINVAL, "state buffer needs %zu bytes, got %zu", need, bytes);
+    char* p = (char*)buf;
+    uint32_t hdr[4] = {kStateMagic, (uint32_t)c->precision, (uint32_t)c->n, (uint32_t)c->total_elems};
+    memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    memcpy(p, &c->steps, sizeof(long long));
+    p += sizeof(long long);
+    for (int l = 0; l < c->n; ++l) {
+        memcpy(p, &c->lats[l].rho_ref, sizeof(double));
+        p += sizeof(double);
+    }
+    CK(cudaMemcpyAsync(p, c->f[c->cur], (size_t)c->total_elems * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lbm_state_size(c, &need);
+    if (rc) return rc;
+    if (!buf || bytes < need) return fail(LBM_EINVAL, "state blob has %zu bytes, need %zu", bytes, need);
+    const char* p = (const char*)buf;
+    uint32_t hdr[4];
+    memcpy(hdr, p, sizeof(hdr));
+    p += sizeof(hdr);
+    if (hdr[0] != kStateMagic || hdr[1] != (uint32_t)c->precision || hdr[2] != (uint32_t)c->n ||
+        hdr[3] != (uint32_t)c->total_elems)
+        return fail(LBM_EINVAL, "state blob does not match this context (lattices or precision differ)");
+    long long steps;
+    memcpy(&steps, p, sizeof(long long));
+    p += sizeof(long long);
+    for (int l = 0; l < c->n; ++l) {
+        memcpy(&c->lats[l].rho_ref, p, sizeof(double));
+        c->lats[l].rho_ref_auto = false;
+        p += sizeof(double);
+    }
+    rc = upload_phys(c);
+    if (rc) return rc;
+    drop_graphs(c);
+    CK(cudaMemcpyAsync(c->f[c->cur], p, (size_t)c->total_elems * c->elem, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->steps = steps;
+    return LBM_OK;
+}
+
+int lbm_tile_count(void) { return kTileCount; }
+
+int lbm_tile_shape(int index, int* tx, int* ty) {
+    if (index < 0 || index >= kTileCount) return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, kTileCount);
+    if (tx) *tx = kTiles[index][0];
+    if (ty) *ty = kTiles[index][1];
+    return LBM_OK;
+}
+
+int lbm_set_tile(lbm_ctx* c, int index) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (index < 0 || index >= kTileCount) return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, kTileCount);
+    if (index == c->tile_index) return LBM_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    return build_tiles(c, index);
+}
+
+int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (steps < 1) return fail(LBM_EINVAL, "steps=%d must be >= 1", steps);
+    const size_t fbytes = (size_t)c->total_elems * c->elem;
+    void* saved = nullptr;
+    int rc = dev_alloc(c, &saved, fbytes);
+    if (rc) return rc;
+    std::vector<unsigned> saved_status(c->n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int cur0 = c->cur;
+    const long long steps0 = c->steps;
+    const int tile0 = c->tile_index;
+    int best = tile0;
+    double best_ms = 1e300;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(saved);
+        c->device_bytes -= fbytes;
+    };
+    cudaError_t e = cudaMemcpyAsync(saved, c->f[cur0], fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(saved_status.data(), c->d_status, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "autotune set-up");
+    }
+    for (int t = 0; t < kTileCount; ++t) {
+        rc = build_tiles(c, t);
+        if (rc) break;
+        // warm-up launch, then the timed steps
+        e = launch_one_step(c, c->cur);
+        c->launches += 1;
+        c->cur ^= 1;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            e = launch_one_step(c, c->cur);
+            c->launches += 1;
+            c->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t_ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune trial");
+            break;
+        }
+        const double per = (double)t_ms / steps;
+        if (ms) ms[t] = per;
+        if (per < best_ms) {
+            best_ms = per;
+            best = t;
+        }
+        // restore the state for the next candidate
+        e = cudaMemcpyAsync(c->f[cur0], saved, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+        c->cur = cur0;
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune restore");
+            break;
+        }
+    }
+    if (!rc) {
+        e = cudaMemcpyAsync(c->f[cur0], saved, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_status, saved_status.data(), c->n * sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "autotune final restore");
+    }
+    c->cur = cur0;
+    c->steps = steps0;
+    cleanup();
+    if (rc) {
+        build_tiles(c, tile0);
+        return rc;
+    }
+    rc = build_tiles(c, best);
+    if (rc) return rc;
+    if (best_index) *best_index = best;
+    return LBM_OK;
+}
+
+int lbm_info(lbm_ctx* c, lbm_info_t* info) {
+    if (!c || !info) return fail(LBM_EINVAL, "null argument");
+    info->n_lattices = c->n;
+    info->precision = c->precision;
+    info->nodes = c->total_nodes;
+    info->fluid_nodes = c->fluid_nodes;
+    info->steps = c->steps;
+    info->kernel_launches = c->launches;
+    info->device_bytes = c->device_bytes;
+    info->tile_x = kTiles[c->tile_index][0];
+    info->tile_y = kTiles[c->tile_index][1];
+    info->n_tiles = c->n_tiles;
+    info->graph_chunk = kGraphChunk;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// Device-side data layout and per-node arithmetic of the D2Q9 pseudopotential
+// MRT step (Shan et al., arXiv:1605.01800, Sec. 2).
+//
+// Layout in HBM (one array per ping-pong buffer, all lattices of a batch):
+//   lattice L owns 9 planes starting at element geom[L].f_off; plane a holds
+//   f_a (or its deviation f_a - w_a rho_ref) at element a*plane + y*pitch + x,
+//   pitch = round_up(nx, 32) so that every row starts on a 128-byte boundary.
+//   The wall mask uses the same y*pitch + x indexing at geom[L].mask_off.
+//
+// Velocity numbering (weights of Eq. 7: axis 1-4, diagonal 5-8):
+//   e0 (0,0) e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1)
+//   e5 (1,1) e6 (-1,1) e7 (-1,-1) e8 (1,-1)
+// Moment order (Eq. 4): rho, e, zeta, j_x, q_x, j_y, q_y, p_xx, p_xy.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr unsigned FLAG_PSI_CLAMPED = 1u;
+constexpr unsigned FLAG_NONFINITE = 2u;
+
+// Geometry of one lattice of the batch.
+struct Geom {
+    int nx, ny, pitch, has_mask;
+    long long f_off;     // element offset of plane 0 in the distribution arrays
+    long long plane;     // elements per plane (ny * pitch)
+    long long mask_off;  // byte offset of this lattice's mask rows
+    long long node_off;  // offset of this lattice in concatenated host arrays
+};
+
+// Physical parameters of one lattice in the arithmetic type T.
+template <typename T>
+struct Phys {
+    T rho_ref;            // deviation reference (0 for plain storage)
+    T RT, a, b4;          // Eq. 15: R*T, a, b/4
+    T G;                  // Eq. 7 / Eq. 13 interaction strength
+    T kpsi;               // 2 / (G c^2) of Eq. 13
+    T cs2;                // lattice sound speed squared, 1/3
+    T s[9];               // diagonal of Lambda, Eq. 2
+    T li_e, li_z;         // s_e * 0.75 eps and s_zeta * 0.75 eps (Li's term after (1 - s/2))
+};
+
+// One CTA's piece of work: a tile of lattice `lat` with origin (x0, y0).
+struct Tile {
+    int lat, x0, y0, pad;
+};
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// psi of Eq. 13 with the CS pressure of Eq. 15, written as
+// psi^2 = kpsi * rho * (R T Z(eta) - a rho - c_s^2), Z = (1+h+h^2-h^3)/(1-h)^3.
+// Near the density where psi^2 = 0 the bracket cancels; the FP32 version
+// recomputes it in FP64 there. psi^2 < 0 is clamped to 0 and flagged.
+__device__ __forceinline__ double psi_bracket_fp64(double rho, double RT, double a,
+                                                   double b4, double cs2) {
+    double eta = b4 * rho;
+    double om = 1.0 - eta;
+    double num = 1.0 + eta * (1.0 + eta * (1.0 - eta));
+    return RT * (num / (om * om * om)) - a * rho - cs2;
+}
+
+__device__ __forceinline__ float psi_of(float rho, const Phys<float>& P, unsigned& flag) {
+    float eta = P.b4 * rho;
+    float om = 1.0f - eta;
+    float num = 1.0f + eta * (1.0f + eta * (1.0f - eta));
+    float q = P.RT * __fdiv_rn(num, om * om * om) - P.a * rho - P.cs2;
+    if (fabsf(q) < 0.0078125f * P.cs2)
+        q = (float)psi_bracket_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b4,
+                                    (double)P.cs2);
+    float psi2 = P.kpsi * rho * q;
+    if (!(psi2 >= 0.0f)) {
+        flag |= (psi2 < 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
+        psi2 = 0.0f;
+    } else if (psi2 > 3.0e38f) {
+        flag |= FLAG_NONFINITE;
+    }
+    return __fsqrt_rn(psi2);
+}
+
+__device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsigned& flag) {
+    double q = psi_bracket_fp64(rho, P.RT, P.a, P.b4, P.cs2);
+    double psi2 = P.kpsi * rho * q;
+    if (!(psi2 >= 0.0)) {
+        flag |= (psi2 < 0.0) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
+        psi2 = 0.0;
+    } else if (psi2 > 1.0e300) {
+        flag |= FLAG_NONFINITE;
+    }
+    return sqrt(psi2);
+}
+
+// Gather the distribution of node (x, y) after streaming (Eq. 5) from the
+// post-collision array `fin` (pull form): f_a(x) = f*_a(x - e_a), periodic; if
+// x - e_a is solid the link is reflected: f_a(x) = f*_abar(x). Coordinates are
+// already wrapped into the lattice. Returns true if (x, y) itself is solid
+// (then f is not filled).
+template <typename T>
+__device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8_t* __restrict__ mask,
+                                          int plane, int pitch, int nx, int ny, int x, int y, T f[9]) {
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    const int r0 = y * pitch;
+    const int rm = ((y == 0) ? ny - 1 : y - 1) * pitch;
+    const int rp = ((y == ny - 1) ? 0 : y + 1) * pitch;
+    if (mask != nullptr) {
+        if (mask[r0 + x]) return true;
+        const int c = r0 + x;
+        f[0] = fin[c];
+        f[1] = mask[r0 + xm] ? fin[3 * plane + c] : fin[1 * plane + r0 + xm];
+        f[2] = mask[rm + x]  ? fin[4 * plane + c] : fin[2 * plane + rm + x];
+        f[3] = mask[r0 + xp] ? fin[1 * plane + c] : fin[3 * plane + r0 + xp];
+        f[4] = mask[rp + x]  ? fin[2 * plane + c] : fin[4 * plane + rp + x];
+        f[5] = mask[rm + xm] ? fin[7 * plane + c] : fin[5 * plane + rm + xm];
+        f[6] = mask[rm + xp] ? fin[8 * plane + c] : fin[6 * plane + rm + xp];
+        f[7] = mask[rp + xp] ? fin[5 * plane + c] : fin[7 * plane + rp + xp];
+        f[8] = mask[rp + xm] ? fin[6 * plane + c] : fin[8 * plane + rp + xm];
+        return false;
+    }
+    f[0] = fin[r0 + x];
+    f[1] = fin[1 * plane + r0 + xm];
+    f[2] = fin[2 * plane + rm + x];
+    f[3] = fin[3 * plane + r0 + xp];
+    f[4] = fin[4 * plane + rp + x];
+    f[5] = fin[5 * plane + rm + xm];
+    f[6] = fin[6 * plane + rm + xp];
+    f[7] = fin[7 * plane + rp + xp];
+    f[8] = fin[8 * plane + rp + xm];
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T sum9(const T f[9]) {
+    return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+}
+
+// Collision of one fluid node in moment space (Eq. 3) with m_eq of Eq. 4,
+// the velocity of Eq. 6 and Li's source of Eq. 14, followed by f* = M^-1 m*.
+// f holds the stored deviation f_a - w_a rho_ref on entry and the
+// post-collision deviation on exit (M w = (1, -2, 1, 0, ...), so the constant
+// part cancels in m - m_eq and M^-1 maps it back). drho = rho - rho_ref.
+// (Fx, Fy) = -G psi (gx, gy) with g = sum_a w_a psi(x + e_a) e_a (Eq. 7);
+// |F|^2 / psi^2 of Eq. 14 is G^2 |g|^2, and (1 - s/2) / (tau - 1/2) = s, so
+// Li's terms enter m* as +s_e 0.75 eps G^2 |g|^2 and -s_zeta 0.75 eps G^2 |g|^2.
+template <typename T>
+__device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G2,
+                                        const Phys<T>& P) {
+    const T half = T(0.5);
+    // first moments and velocity, Eq. 6
+    const T sx = f[1] - f[3];
+    const T sy = f[2] - f[4];
+    const T d58 = f[5] - f[7];
+    const T d68 = f[6] - f[8];
+    const T jx = sx + d58 - d68;
+    const T jy = sy + d58 + d68;
+    const T rvx = jx + half * Fx;       // rho v_x
+    const T rvy = jy + half * Fy;
+    const T inv_rho = T(1) / rho;
+    const T vx = rvx * inv_rho;
+    const T vy = rvy * inv_rho;
+
+    // m = M f (deviation)
+    const T a14 = (f[1] + f[3]) + (f[2] + f[4]);
+    const T d58p = (f[5] + f[7]) + (f[6] + f[8]);
+    const T m1 = -T(4) * f[0] - a14 + T(2) * d58p;
+    const T m2 = T(4) * f[0] - T(2) * a14 + d58p;
+    const T m4 = -T(2) * sx + d58 - d68;
+    const T m6 = -T(2) * sy + d58 + d68;
+    const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
+    const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
+
+    // m_eq of Eq. 4 (deviation form: the rho_ref parts of rho, e, zeta cancel)
+    const T ru2 = rvx * vx + rvy * vy;  // rho |v|^2
+    const T meq1 = -T(2) * drho + T(3) * ru2;
+    const T meq2 = drho - T(3) * ru2;
+    const T meq4 = -rvx;
+    const T meq6 = -rvy;
+    const T meq7 = rvx * vx - rvy * vy;
+    const T meq8 = rvx * vy;
+
+    // source S of Eq. 14 (Eq. 8 plus Li's terms)
+    const T vF = vx * Fx + vy * Fy;
+    const T li = g2G2;
+    // m* = m - s (m - m_eq) + (1 - s/2) S
+    const T ms0 = drho;
+    const T ms1 = m1 - P.s[1] * (m1 - meq1) + (T(1) - half * P.s[1]) * (T(6) * vF) + P.li_e * li;
+    const T ms2 = m2 - P.s[2] * (m2 - meq2) - (T(1) - half * P.s[2]) * (T(6) * vF) - P.li_z * li;
+    const T ms3 = jx - P.s[3] * (jx - rvx) + (T(1) - half * P.s[3]) * Fx;
+    const T ms4 = m4 - P.s[4] * (m4 - meq4) - (T(1) - half * P.s[4]) * Fx;
+    const T ms5 = jy - P.s[5] * (jy - rvy) + (T(1) - half * P.s[5]) * Fy;
+    const T ms6 = m6 - P.s[6] * (m6 - meq6) - (T(1) - half * P.s[6]) * Fy;
+    const T ms7 = m7 - P.s[7] * (m7 - meq7) + (T(1) - half * P.s[7]) * (T(2) * (vx * Fx - vy * Fy));
+    const T ms8 = m8 - P.s[8] * (m8 - meq8) + (T(1) - half * P.s[8]) * (vx * Fy + vy * Fx);
+
+    // f* = M^-1 m* = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
+    const T a0 = ms0 * T(1.0 / 9.0);
+    const T a1 = ms1 * T(1.0 / 36.0);
+    const T a2 = ms2 * T(1.0 / 36.0);
+    const T a3 = ms3 * T(1.0 / 6.0);
+    const T a4 = ms4 * T(1.0 / 12.0);
+    const T a5 = ms5 * T(1.0 / 6.0);
+    const T a6 = ms6 * T(1.0 / 12.0);
+    const T a7 = ms7 * T(0.25);
+    const T a8 = ms8 * T(0.25);
+    const T axis = a0 - a1 - T(2) * a2;
+    const T diag = a0 + T(2) * a1 + a2;
+    const T px = a3 - T(2) * a4;
+    const T py = a5 - T(2) * a6;
+    const T qx = a3 + a4;
+    const T qy = a5 + a6;
+    f[0] = a0 - T(4) * a1 + T(4) * a2;
+    f[1] = axis + px + a7;
+    f[2] = axis + py - a7;
+    f[3] = axis - px + a7;
+    f[4] = axis - py - a7;
+    f[5] = diag + qx + qy + a8;
+    f[6] = diag - qx + qy - a8;
+    f[7] = diag - qx - qy + a8;
+    f[8] = diag + qx - qy - a8;
+}
+
+// Force sum g = sum_a w_a psi(x + e_a) e_a of Eq. 7 from the nine psi values
+// of a 3x3 neighbourhood (p[dy+1][dx+1]); a negative entry marks a solid
+// neighbour, which takes the centre node's psi.
+template <typename T>
+__device__ __forceinline__ void force_sum(T c, T pe, T pn, T pw, T ps, T pne, T pnw, T psw,
+                                          T pse, T& gx, T& gy) {
+    pe = pe < T(0) ? c : pe;
+    pn = pn < T(0) ? c : pn;
+    pw = pw < T(0) ? c : pw;
+    ps = ps < T(0) ? c : ps;
+    pne = pne < T(0) ? c : pne;
+    pnw = pnw < T(0) ? c : pnw;
+    psw = psw < T(0) ? c : psw;
+    pse = pse < T(0) ? c : pse;
+    const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0);
+    gx = third * (pe - pw) + twelfth * ((pne - pnw) + (pse - psw));
+    gy = third * (pn - ps) + twelfth * ((pne + pnw) - (psw + pse));
+}
+
+}  // namespace lbm

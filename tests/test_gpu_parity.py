@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  - FP64 storage: the GPU and the oracle evaluate the same formulas in a
+    different order, so densities agree to a few ulps per step; 1e-12
+    relative after up to tens of steps, 1e-10 after 3000 steps of a static
+    droplet.
+  - FP32 storage (deviation or plain): density within 1e-4 relative of the
+    oracle at every fluid node, the target the method's FP32 path is held to.
+    Velocities are compared against 1e-4 of the FP64 result's scale.
+  - Layout choices (tile shape, batching, graph replay, checkpoints) must not
+    change a single bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import d2q9, thermo
+from paper_1605_01800_gb300 import inputs, lbm
+from tests.cases import abs_err, fluid, oracle_from_spec, rel_err, small_spec
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    dict(nx=1, ny=1), dict(nx=3, ny=1), dict(nx=5, ny=3), dict(nx=4, ny=4),
+    dict(nx=37, ny=29), dict(nx=130, ny=9), dict(nx=64, ny=48, walls=True),
+    dict(nx=33, ny=17, walls=True), dict(nx=7, ny=3, walls=True),
+]
+
+
+def _ids(c):
+    return f"{c['nx']}x{c['ny']}{'w' if c.get('walls') else ''}"
+
+
+def run_gpu(specs, precision, steps, tile=None, stream=None):
+    b = lbm.Batch(specs, precision, stream=stream)
+    if tile is not None:
+        lbm.lbm_set_tile(b.ctx, tile)
+    b.init()
+    b.step(steps)
+    out = [b.moments(i, allow_flags=True) for i in range(len(specs))]
+    b.close()
+    return out
+
+
+def run_oracle(spec, steps):
+    L = oracle_from_spec(spec)
+    L.step(steps)
+    return L.moments(), L
+
+
+@pytest.mark.parametrize("case", SMALL, ids=_ids)
+@pytest.mark.parametrize("steps", [1, 9])
+def test_fp64_matches_oracle(case, steps):
+    spec = small_spec(case["nx"], case["ny"], walls=case.get("walls", False))
+    (rho, ux, uy, p), = run_gpu([spec], "fp64", steps)
+    (orho, oux, ouy, op), _ = run_oracle(spec, steps)
+    m = fluid(spec)
+    assert rel_err(rho, orho, m) < 1e-12
+    assert abs_err(ux, oux, m) < 1e-13 and abs_err(uy, ouy, m) < 1e-13
+    assert rel_err(p, op, m) < 1e-11
+
+
+@pytest.mark.parametrize("case", SMALL, ids=_ids)
+@pytest.mark.parametrize("precision", ["fp32_dev", "fp32"])
+def test_fp32_matches_oracle(case, precision):
+    steps = 9
+    spec = small_spec(case["nx"], case["ny"], walls=case.get("walls", False))
+    (rho, ux, uy, p), = run_gpu([spec], precision, steps)
+    (orho, oux, ouy, op), _ = run_oracle(spec, steps)
+    m = fluid(spec)
+    assert rel_err(rho, orho, m) < 1e-4
+    uscale = max(np.abs(oux).max(), np.abs(ouy).max(), 1e-3)
+    assert abs_err(ux, oux, m) < 1e-4 * uscale and abs_err(uy, ouy, m) < 1e-4 * uscale
+
+
+@pytest.mark.parametrize("precision", ["fp32_dev", "fp64"])
+def test_every_tile_is_bitwise_identical(precision):
+    specs = [small_spec(70, 45, walls=True), small_spec(19, 23)]
+    ref = run_gpu(specs, precision, 5, tile=0)
+    for t in range(1, lbm.lbm_tile_count()):
+        got = run_gpu(specs, precision, 5, tile=t)
+        for a, b in zip(ref, got):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), f"tile {lbm.lbm_tile_shape(t)}"
+
+
+def test_batch_equals_individual_runs():
+    specs = [small_spec(40, 30, seed=1), small_spec(97, 31, walls=True, seed=2),
+             small_spec(16, 80, seed=3, shape="bubble"), small_spec(5, 3, seed=4)]
+    batched = run_gpu(specs, "fp32_dev", 12)
+    for i, s in enumerate(specs):
+        (alone,) = run_gpu([s], "fp32_dev", 12)
+        for x, y in zip(batched[i], alone):
+            assert np.array_equal(x, y)
+
+
+def test_graph_replay_equals_single_launches():
+    torch = pytest.importorskip("torch")
+    specs = [small_spec(50, 41, walls=True), small_spec(33, 33)]
+    direct = run_gpu(specs, "fp32_dev", 70)            # default stream: one launch per step
+    s = torch.cuda.Stream()
+    graphed = run_gpu(specs, "fp32_dev", 70, stream=s)  # 2 graph chunks + 6 launches
+    for a, b in zip(direct, graphed):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_checkpoint_roundtrip_is_bitwise():
+    specs = [small_spec(48, 40, walls=True), small_spec(21, 13)]
+    b = lbm.Batch(specs, "fp32_dev")
+    b.init()
+    b.step(7)
+    blob = lbm.lbm_save_state(b.ctx)
+    b.step(11)
+    first = [b.moments(i) for i in range(2)]
+    assert b.info()["steps"] == 18
+    b2 = lbm.Batch(specs, "fp32_dev")
+    lbm.lbm_load_state(b2.ctx, blob)
+    assert b2.info()["steps"] == 7
+    b2.step(11)
+    second = [b2.moments(i) for i in range(2)]
+    for a, c in zip(first, second):
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y)
+    b3 = lbm.Batch([specs[0]], "fp32_dev")
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_load_state(b3.ctx, blob)
+
+
+def test_autotune_keeps_state_and_results():
+    specs = [small_spec(96, 64, walls=True)]
+    b = lbm.Batch(specs, "fp32_dev")
+    b.init()
+    b.step(3)
+    best, ms = lbm.lbm_autotune(b.ctx, 4)
+    assert 0 <= best < lbm.lbm_tile_count() and all(t > 0 for t in ms)
+    assert b.info()["steps"] == 3
+    b.step(5)
+    got = b.moments(0)
+    (ref,) = run_gpu(specs, "fp32_dev", 8, tile=0)
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)
+
+
+def test_psi_domain_is_flagged_and_clamped():
+    Tc = inputs.critical_temperature()
+    r0 = thermo.psi_root(0.5 * Tc)
+    nx = ny = 8
+    rho = np.full((ny, nx), 0.45)
+    rho[3:5, 3:5] = r0 * 1.01
+    spec = inputs.LatticeSpec(nx, ny, 0.5 * Tc, inputs.relax_rates(0.6), 1.86, rho, rho_ref=0.45)
+    for prec in ("fp32_dev", "fp64"):
+        b = lbm.Batch([spec], prec)
+        b.init()
+        b.step(1)
+        assert b.status(0) & lbm.LBM_FLAG_PSI_CLAMPED
+        out = [np.empty((ny, nx)) for _ in range(4)]
+        rc = lbm.lbm_read_moments(b.ctx, 0, *out, allow_flags=True)
+        assert rc == lbm.LBM_EPSI_DOMAIN
+        lbm.lbm_clear_status(b.ctx)
+        assert b.status(0) == 0
+        b.close()
+    L = oracle_from_spec(spec)
+    assert L.step(1) & d2q9.FLAG_PSI_CLAMPED
+
+
+def test_init_rejects_nonpositive_density():
+    spec = small_spec(8, 8)
+    b = lbm.Batch([spec], "fp32_dev")
+    bad = spec.rho.copy()
+    bad[2, 2] = -0.1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_init_fields(b.ctx, 0, bad)
+    assert e.value.code == lbm.LBM_EINVAL
+
+
+# ---------------------------------------------------------------- workload-sized cases
+
+def test_droplet_128_3000_steps():
+    """128^2 static droplet, T = 0.8 Tc, R = 25, W = 2, 3000 steps."""
+    (spec,) = inputs.droplet_128()
+    steps = 3000
+    (orho, oux, ouy, op), L = run_oracle(spec, steps)
+    assert L.flags == 0
+    (rho64, ux64, uy64, p64), = run_gpu([spec], "fp64", steps)
+    assert rel_err(rho64, orho) < 1e-10
+    (rho32, ux32, uy32, p32), = run_gpu([spec], "fp32_dev", steps)
+    assert rel_err(rho32, orho) < 1e-4
+    uscale = max(np.abs(oux).max(), np.abs(ouy).max())
+    assert abs_err(ux32, oux) < 1e-2 * uscale and abs_err(uy32, ouy) < 1e-2 * uscale
+
+
+def test_coexistence_batch_full_size():
+    """32 slabs 256x64: every lattice after 20 steps, FP32 deviation and FP64."""
+    specs = inputs.coexistence_batch()
+    steps = 20
+    g32 = run_gpu(specs, "fp32_dev", steps)
+    g64 = run_gpu(specs, "fp64", steps)
+    for i, spec in enumerate(specs):
+        (orho, oux, ouy, op), L = run_oracle(spec, steps)
+        assert L.flags == 0
+        assert rel_err(g64[i][0], orho) < 1e-12, i
+        assert rel_err(g32[i][0], orho) < 1e-4, i
+
+
+def test_coexistence_batch_mass_conserved():
+    specs = inputs.coexistence_batch()
+    for prec, tol in (("fp32_dev", 1e-6), ("fp64", 1e-12)):
+        b = lbm.Batch(specs, prec)
+        b.init()
+        m0 = [b.mass(i) for i in range(len(specs))]
+        ref = [oracle_from_spec(s).mass() for s in specs[:4]]
+        for i in range(4):
+            assert m0[i] == pytest.approx(ref[i], rel=1e-7 if prec != "fp64" else 1e-13)
+        b.step(2000)
+        for i in range(len(specs)):
+            assert abs(b.mass(i) / m0[i] - 1) < tol, (prec, i)
+        assert b.info()["steps"] == 2000
+        b.close()
+
+
+def test_laplace_batch_full_size_sampled():
+    """48 uneven droplets (128^2 .. 320^2) in one batch; the oracle checks the
+    smallest, a middle and the largest lattice."""
+    specs = inputs.laplace_batch()
+    steps = 4
+    g = run_gpu(specs, "fp32_dev", steps)
+    for i in (0, 23, 47):
+        (orho, _, _, _), _ = run_oracle(specs[i], steps)
+        assert rel_err(g[i][0], orho) < 1e-4, i
+
+
+def test_cavitation_1024_full_size():
+    (spec,) = inputs.cavitation_1024()
+    steps = 3
+    (g,) = run_gpu([spec], "fp32_dev", steps)
+    (orho, _, _, _), _ = run_oracle(spec, steps)
+    assert rel_err(g[0], orho) < 1e-4
+
+
+def test_collapse_walls_full_size():
+    (spec,) = inputs.collapse()
+    steps = 3
+    (orho, _, _, _), L = run_oracle(spec, steps)
+    m = fluid(spec)
+    (g64,) = run_gpu([spec], "fp64", steps)
+    assert rel_err(g64[0], orho, m) < 1e-12
+    (g32,) = run_gpu([spec], "fp32_dev", steps)
+    assert rel_err(g32[0], orho, m) < 1e-4
+    assert np.all(g32[0][~m] == 0)
