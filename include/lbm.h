@@ -74,9 +74,12 @@ typedef struct {
  *              (rho, e, zeta, j_x, q_x, j_y, q_y, p_xx, p_xy); each in [0, 2).
  *   eps        epsilon of Li's term, Eq. 14.
  *   rho_ref    FP32_DEV only: the reference density of the stored deviation
- *              f_a - w_a rho_ref. > 0: used as given; 0: plain FP32 storage;
- *              < 0: taken as the maximum of the first density field passed to
- *              lbm_init_fields*. Ignored for LBM_FP32 and LBM_FP64.
+ *              f_a - w_a rho_ref (rounded to FP32). > 0: used as given;
+ *              0: plain FP32 storage; < 0: taken as the minimum of the first
+ *              density field passed to lbm_init_fields* over fluid nodes.
+ *              Any 0 <= rho_ref <= min(rho) stores every node at least as
+ *              precisely as plain FP32, and the vapour of a two-phase field
+ *              far more precisely. Ignored for LBM_FP32 and LBM_FP64.
  *   wall_mask  NULL (no solid nodes) or nx*ny bytes, nonzero = solid node. It
  *              is copied. Solid nodes are not updated; a fluid node's link
  *              that would stream into a solid node is reflected (halfway
@@ -107,14 +110,15 @@ typedef struct {
 
 /* Create a one-lattice context (the paper's single-domain runs, Sec. 3-4).
  * eps is the epsilon of Eq. 14; relax_rates the nine rates of Eq. 2. For
- * LBM_FP32_DEV the deviation reference is the maximum of the first density
+ * LBM_FP32_DEV the deviation reference is the minimum of the first density
  * field given to lbm_init_fields. The context starts in the rest state
  * rho = 0 until lbm_init_fields is called. */
 int lbm_create(int nx, int ny, const lbm_eos_params* eos, const double relax_rates[9],
                double eps, const uint8_t* wall_mask, int precision, lbm_ctx** out);
 
-/* Create a context advancing n independent lattices of any sizes together:
- * each lbm_step advances every lattice by one time step in one launch. */
+/* Create a context advancing n (1 <= n <= 65535) independent lattices of any
+ * sizes together: each lbm_step advances every lattice by one time step in one
+ * launch. */
 int lbm_create_batch(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** out);
 
 /* Run the context's work on `cuda_stream` (a cudaStream_t, e.g. PyTorch's

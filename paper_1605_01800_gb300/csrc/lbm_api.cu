@@ -42,8 +42,6 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 constexpr double kCs2 = 1.0 / 3.0;
-constexpr double kWeq[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                            1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 constexpr int kGraphChunk = 32;  // steps per captured graph (even: parity is preserved)
 constexpr uint32_t kStateMagic = 0x4c424d31u;  // "LBM1"
 
@@ -80,7 +78,7 @@ struct lbm_ctx {
     unsigned* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_scalar = nullptr;
-    double* d_io = nullptr;      // staging: 4 * max_nodes doubles
+    double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
     std::vector<Phys<double>> phys_d;
     size_t device_bytes = 0;
 
@@ -123,7 +121,10 @@ void fill_phys(const HostLattice& L, Phys<double>& P) {
     P.G = d.eos.G;
     P.kpsi = 2.0 / d.eos.G;  // c = 1
     P.cs2 = kCs2;
-    for (int k = 0; k < 9; ++k) P.s[k] = d.s[k];
+    for (int k = 0; k < 9; ++k) {
+        P.s[k] = d.s[k];
+        P.h[k] = 1.0 - 0.5 * d.s[k];
+    }
     P.li_e = d.s[1] * 0.75 * d.eps;
     P.li_z = d.s[2] * 0.75 * d.eps;
 }
@@ -136,7 +137,10 @@ void to_float(const Phys<double>& D, Phys<float>& F) {
     F.G = (float)D.G;
     F.kpsi = (float)D.kpsi;
     F.cs2 = (float)D.cs2;
-    for (int k = 0; k < 9; ++k) F.s[k] = (float)D.s[k];
+    for (int k = 0; k < 9; ++k) {
+        F.s[k] = (float)D.s[k];
+        F.h[k] = (float)D.h[k];
+    }
     F.li_e = (float)D.li_e;
     F.li_z = (float)D.li_z;
 }
@@ -181,7 +185,7 @@ void free_ctx(lbm_ctx* c) {
 // Work-list of one step launch: every tile of every lattice, lattices in
 // creation order, tiles row-major within a lattice.
 int build_tiles(lbm_ctx* c, int tile_index) {
-    const int tx = kTiles[tile_index][0], ty = kTiles[tile_index][1];
+    const int tx = kTiles[tile_index][0], ty = kTiles[tile_index][1] * kTiles[tile_index][2];
     std::vector<Tile> tiles;
     for (int l = 0; l < c->n; ++l) {
         const Geom& g = c->lats[l].geom;
@@ -276,63 +280,98 @@ int read_status(lbm_ctx* c, std::vector<unsigned>& out) {
     return LBM_OK;
 }
 
-int init_one(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy) {
+// Validate lattice `lat`'s host fields (fluid nodes only) and resolve an
+// automatic FP32 deviation reference (minimum density).
+int check_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy,
+                 bool* phys_changed) {
     HostLattice& L = c->lats[lat];
-    const Geom& g = L.geom;
-    const long long n = (long long)g.nx * g.ny;
+    const long long n = (long long)L.geom.nx * L.geom.ny;
     const uint8_t* m = L.mask.empty() ? nullptr : L.mask.data();
-    double rmax = 0.0;
+    double rmin = HUGE_VAL;
     for (long long i = 0; i < n; ++i) {
         if (m && m[i]) continue;
         if (!(std::isfinite(rho[i]) && rho[i] > 0.0))
             return fail(LBM_EINVAL, "lattice %d: rho[%lld]=%g must be finite and > 0", lat, i, rho[i]);
         if ((ux && !std::isfinite(ux[i])) || (uy && !std::isfinite(uy[i])))
             return fail(LBM_EINVAL, "lattice %d: velocity at %lld is not finite", lat, i);
-        rmax = std::max(rmax, rho[i]);
+        rmin = std::min(rmin, rho[i]);
     }
     if (c->precision == LBM_FP32_DEV && L.rho_ref_auto) {
-        L.rho_ref = (double)(float)rmax;
+        L.rho_ref = std::isfinite(rmin) ? (double)(float)rmin : 0.0;
         L.rho_ref_auto = false;
+        *phys_changed = true;
+    }
+    return LBM_OK;
+}
+
+LaunchSet launch_set(lbm_ctx* c, int lat0, int n_lat) {
+    long long mx = 0;
+    for (int l = lat0; l < lat0 + n_lat; ++l)
+        mx = std::max(mx, (long long)c->lats[l].geom.nx * c->lats[l].geom.ny);
+    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx};
+}
+
+long long range_nodes(lbm_ctx* c, int lat0, int n_lat) {
+    const Geom& last = c->lats[lat0 + n_lat - 1].geom;
+    return last.node_off + (long long)last.nx * last.ny - c->lats[lat0].geom.node_off;
+}
+
+// Initial state of lattices [lat0, lat0 + n_lat) from host arrays that start
+// at lattice lat0's first node: one upload per field, one kernel launch.
+int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double* ux, const double* uy) {
+    bool changed = false;
+    for (int l = lat0; l < lat0 + n_lat; ++l) {
+        const long long o = c->lats[l].geom.node_off - c->lats[lat0].geom.node_off;
+        int rc = check_fields(c, l, rho + o, ux ? ux + o : nullptr, uy ? uy + o : nullptr, &changed);
+        if (rc) return rc;
+    }
+    if (changed) {
         int rc = upload_phys(c);
         if (rc) return rc;
         drop_graphs(c);
     }
-    double* d_rho = c->d_io;
-    double* d_ux = ux ? c->d_io + c->max_nodes : nullptr;
-    double* d_uy = uy ? c->d_io + 2 * c->max_nodes : nullptr;
-    CK(cudaMemcpyAsync(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (ux) CK(cudaMemcpyAsync(d_ux, ux, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (uy) CK(cudaMemcpyAsync(d_uy, uy, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    const uint8_t* dm = L.mask.empty() ? nullptr : c->d_mask + g.mask_off;
+    const long long base = c->lats[lat0].geom.node_off;
+    const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
+    double* d_rho = c->d_io + base;
+    double* d_ux = ux ? c->d_io + c->total_nodes + base : nullptr;
+    double* d_uy = uy ? c->d_io + 2 * c->total_nodes + base : nullptr;
+    CK(cudaMemcpyAsync(d_rho, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (ux) CK(cudaMemcpyAsync(d_ux, ux, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (uy) CK(cudaMemcpyAsync(d_uy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
+    const LaunchSet ls = launch_set(c, lat0, n_lat);
     cudaError_t e;
     if (c->precision == LBM_FP64)
-        e = launch_init_f64(g, L.rho_ref, d_rho, d_ux, d_uy, dm, (double*)c->f[c->cur], c->stream);
+        e = launch_init_f64(ls, c->d_io, ux ? c->d_io + c->total_nodes : nullptr,
+                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (double*)c->f[c->cur], c->stream);
     else
-        e = launch_init_f32(g, (float)L.rho_ref, d_rho, d_ux, d_uy, dm, (float*)c->f[c->cur], c->stream);
+        e = launch_init_f32(ls, c->d_io, ux ? c->d_io + c->total_nodes : nullptr,
+                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (float*)c->f[c->cur], c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     c->launches += 1;
-    // the staging buffer is reused by the next call: wait for the copies
+    // the host arrays may be pageable and the staging buffer is reused: wait
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
-int moments_one(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, double* p) {
-    const HostLattice& L = c->lats[lat];
-    const Geom& g = L.geom;
-    const long long n = (long long)g.nx * g.ny;
-    double* d[4] = {rho ? c->d_io : nullptr, ux ? c->d_io + c->max_nodes : nullptr,
-                    uy ? c->d_io + 2 * c->max_nodes : nullptr, p ? c->d_io + 3 * c->max_nodes : nullptr};
-    const uint8_t* dm = L.mask.empty() ? nullptr : c->d_mask + g.mask_off;
+// rho, v, p of lattices [lat0, lat0 + n_lat) into host arrays that start at
+// lattice lat0's first node: one kernel launch, one download per field.
+int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, double* uy, double* p) {
+    const long long N = c->total_nodes;
+    double* d[4] = {rho ? c->d_io : nullptr, ux ? c->d_io + N : nullptr, uy ? c->d_io + 2 * N : nullptr,
+                    p ? c->d_io + 3 * N : nullptr};
+    const LaunchSet ls = launch_set(c, lat0, n_lat);
     cudaError_t e;
     if (c->precision == LBM_FP64)
-        e = launch_moments_f64(g, c->phys_d[lat], (const double*)c->f[c->cur], dm, d[0], d[1], d[2], d[3], c->stream);
+        e = launch_moments_f64(ls, (const double*)c->f[c->cur], d[0], d[1], d[2], d[3], c->stream);
     else
-        e = launch_moments_f32(g, c->phys_d[lat], (const float*)c->f[c->cur], dm, d[0], d[1], d[2], d[3], c->stream);
+        e = launch_moments_f32(ls, (const float*)c->f[c->cur], d[0], d[1], d[2], d[3], c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
     c->launches += 1;
+    const long long base = c->lats[lat0].geom.node_off;
+    const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
     double* h[4] = {rho, ux, uy, p};
     for (int k = 0; k < 4; ++k)
-        if (h[k]) CK(cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (h[k]) CK(cudaMemcpyAsync(h[k], d[k] + base, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -341,6 +380,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (!out) return fail(LBM_EINVAL, "out is null");
     *out = nullptr;
     if (n < 1 || !desc) return fail(LBM_EINVAL, "need n >= 1 lattice descriptions");
+    if (n > 65535) return fail(LBM_EINVAL, "n=%d lattices: at most 65535 per context", n);
     if (precision != LBM_FP32_DEV && precision != LBM_FP32 && precision != LBM_FP64)
         return fail(LBM_EINVAL, "unknown precision %d", precision);
     for (int i = 0; i < n; ++i) {
@@ -414,7 +454,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (!rc) rc = dev_alloc(c, &c->d_status, n * sizeof(unsigned));
     if (!rc) rc = dev_alloc(c, &c->d_partials, kMassBlocks * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_scalar, sizeof(double));
-    if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->max_nodes * sizeof(double));
+    if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->total_nodes * sizeof(double));
     if (rc) {
         free_ctx(c);
         return rc;
@@ -470,7 +510,7 @@ int lbm_create(int nx, int ny, const lbm_eos_params* eos, const double relax_rat
     d.eos = *eos;
     for (int k = 0; k < 9; ++k) d.s[k] = relax_rates[k];
     d.eps = eps;
-    d.rho_ref = -1.0;  // FP32_DEV: maximum of the first density field
+    d.rho_ref = -1.0;  // FP32_DEV: minimum of the first density field
     d.wall_mask = wall_mask;
     return create_common(1, &d, precision, out);
 }
@@ -494,7 +534,7 @@ int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, co
     int rc = check_lat(c, lat);
     if (rc) return rc;
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
-    rc = init_one(c, lat, rho, ux, uy);
+    rc = init_range(c, lat, 1, rho, ux, uy);
     if (rc) return rc;
     c->steps = 0;
     return LBM_OK;
@@ -503,11 +543,8 @@ int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, co
 int lbm_init_fields_all(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
     if (!c) return fail(LBM_EINVAL, "null context");
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
-    for (int l = 0; l < c->n; ++l) {
-        const long long o = c->lats[l].geom.node_off;
-        int rc = init_one(c, l, rho + o, ux ? ux + o : nullptr, uy ? uy + o : nullptr);
-        if (rc) return rc;
-    }
+    int rc = init_range(c, 0, c->n, rho, ux, uy);
+    if (rc) return rc;
     c->steps = 0;
     return LBM_OK;
 }
@@ -539,7 +576,7 @@ int lbm_step(lbm_ctx* c, int n) {
 int lbm_read_moments(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, double* p) {
     int rc = check_lat(c, lat);
     if (rc) return rc;
-    rc = moments_one(c, lat, rho, ux, uy, p);
+    rc = moments_range(c, lat, 1, rho, ux, uy, p);
     if (rc) return rc;
     std::vector<unsigned> st;
     rc = read_status(c, st);
@@ -549,14 +586,10 @@ int lbm_read_moments(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, d
 
 int lbm_read_moments_all(lbm_ctx* c, double* rho, double* ux, double* uy, double* p) {
     if (!c) return fail(LBM_EINVAL, "null context");
-    for (int l = 0; l < c->n; ++l) {
-        const long long o = c->lats[l].geom.node_off;
-        int rc = moments_one(c, l, rho ? rho + o : nullptr, ux ? ux + o : nullptr,
-                             uy ? uy + o : nullptr, p ? p + o : nullptr);
-        if (rc) return rc;
-    }
+    int rc = moments_range(c, 0, c->n, rho, ux, uy, p);
+    if (rc) return rc;
     std::vector<unsigned> st;
-    int rc = read_status(c, st);
+    rc = read_status(c, st);
     if (rc) return rc;
     unsigned all = 0;
     for (unsigned s : st) all |= s;
@@ -673,7 +706,7 @@ int lbm_tile_count(void) { return kTileCount; }
 int lbm_tile_shape(int index, int* tx, int* ty) {
     if (index < 0 || index >= kTileCount) return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, kTileCount);
     if (tx) *tx = kTiles[index][0];
-    if (ty) *ty = kTiles[index][1];
+    if (ty) *ty = kTiles[index][1] * kTiles[index][2];
     return LBM_OK;
 }
 
@@ -779,7 +812,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->kernel_launches = c->launches;
     info->device_bytes = c->device_bytes;
     info->tile_x = kTiles[c->tile_index][0];
-    info->tile_y = kTiles[c->tile_index][1];
+    info->tile_y = kTiles[c->tile_index][1] * kTiles[c->tile_index][2];
     info->n_tiles = c->n_tiles;
     info->graph_chunk = kGraphChunk;
     return LBM_OK;

@@ -28,9 +28,18 @@ __device__ __forceinline__ double feq(int a, double rho, double ux, double uy) {
 // stored value at node y for population b is f_eq_b of the node y + e_b it
 // streams into, or f_eq_bbar(y) when y + e_b is solid (the reflected link).
 template <typename T>
-__global__ void init_kernel(Geom g, T rho_ref, const double* __restrict__ rho,
-                            const double* __restrict__ ux, const double* __restrict__ uy,
-                            const uint8_t* __restrict__ mask, T* __restrict__ f) {
+__global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
+                            int lat0, const double* __restrict__ rho, const double* __restrict__ ux,
+                            const double* __restrict__ uy, const uint8_t* __restrict__ mask_base,
+                            T* __restrict__ f_base) {
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    const double rho_ref = phys[lat].rho_ref;
+    const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
+    T* f = f_base + g.f_off;
+    rho += g.node_off;
+    if (ux) ux += g.node_off;
+    if (uy) uy += g.node_off;
     const long long n = (long long)g.nx * g.ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -49,7 +58,7 @@ __global__ void init_kernel(Geom g, T rho_ref, const double* __restrict__ rho,
                 const long long j = (long long)yt * g.nx + xt;
                 v = feq(b, rho[j], ux ? ux[j] : 0.0, uy ? uy[j] : 0.0);
             }
-            f[b * g.plane + c] = (T)(v - kWeq[b] * (double)rho_ref);
+            f[b * g.plane + c] = (T)(v - kWeq[b] * rho_ref);
         }
     }
 }
@@ -70,20 +79,27 @@ __device__ __forceinline__ double psi_fp64(double rho, const Phys<double>& P) {
 }
 
 template <typename T>
-__global__ void moments_kernel(Geom g, Phys<double> P, const T* __restrict__ f,
-                               const uint8_t* __restrict__ mask, double* __restrict__ rho_out,
+__global__ void moments_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
+                               int lat0, const T* __restrict__ f_base,
+                               const uint8_t* __restrict__ mask_base, double* __restrict__ rho_out,
                                double* __restrict__ ux_out, double* __restrict__ uy_out,
                                double* __restrict__ p_out) {
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    const Phys<double> P = phys[lat];
+    const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
+    const T* f = f_base + g.f_off;
     const long long n = (long long)g.nx * g.ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
+        const long long o = g.node_off + i;
         const int x = (int)(i % g.nx), y = (int)(i / g.nx);
         double fc[9];
         if (!pulled_fp64<T>(g, f, mask, P.rho_ref, x, y, fc)) {
-            if (rho_out) rho_out[i] = 0.0;
-            if (ux_out) ux_out[i] = 0.0;
-            if (uy_out) uy_out[i] = 0.0;
-            if (p_out) p_out[i] = 0.0;
+            if (rho_out) rho_out[o] = 0.0;
+            if (ux_out) ux_out[o] = 0.0;
+            if (uy_out) uy_out[o] = 0.0;
+            if (p_out) p_out[o] = 0.0;
             continue;
         }
         double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -108,11 +124,11 @@ __global__ void moments_kernel(Geom g, Phys<double> P, const T* __restrict__ f,
             gy += w * pn * kEy[a];
         }
         const double Fx = -P.G * psi * gx, Fy = -P.G * psi * gy;
-        if (rho_out) rho_out[i] = rho;
-        if (ux_out) ux_out[i] = (jx + 0.5 * Fx) / rho;
-        if (uy_out) uy_out[i] = (jy + 0.5 * Fy) / rho;
+        if (rho_out) rho_out[o] = rho;
+        if (ux_out) ux_out[o] = (jx + 0.5 * Fx) / rho;
+        if (uy_out) uy_out[o] = (jy + 0.5 * Fy) / rho;
         // Eq. 10: p = rho c_s^2 + G c^2 psi^2 / 2
-        if (p_out) p_out[i] = rho * P.cs2 + 0.5 * P.G * psi * psi;
+        if (p_out) p_out[o] = rho * P.cs2 + 0.5 * P.G * psi * psi;
     }
 }
 
@@ -149,23 +165,26 @@ __global__ void mass_final_kernel(const double* __restrict__ partials, double rh
     *out = s + rho_ref * (double)n_fluid;
 }
 
+dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
+    long long bx = (max_nodes + threads - 1) / threads;
+    if (bx > 4096) bx = 4096;
+    if (bx < 1) bx = 1;
+    return dim3((unsigned)bx, (unsigned)n_lat);
+}
+
 template <typename T>
-cudaError_t init_impl(const Geom& g, T rho_ref, const double* rho, const double* ux,
-                      const double* uy, const uint8_t* mask, T* f, cudaStream_t s) {
-    const long long n = (long long)g.nx * g.ny;
-    const int threads = 256;
-    const int blocks = (int)((n + threads - 1) / threads < 65535 ? (n + threads - 1) / threads : 65535);
-    init_kernel<T><<<blocks, threads, 0, s>>>(g, rho_ref, rho, ux, uy, mask, f + g.f_off);
+cudaError_t init_impl(const LaunchSet& L, const double* rho, const double* ux, const double* uy,
+                      T* f, cudaStream_t s) {
+    init_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(
+        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t moments_impl(const Geom& g, const Phys<double>& P, const T* f, const uint8_t* mask,
-                         double* rho, double* ux, double* uy, double* p, cudaStream_t s) {
-    const long long n = (long long)g.nx * g.ny;
-    const int threads = 128;
-    const int blocks = (int)((n + threads - 1) / threads < 65535 ? (n + threads - 1) / threads : 65535);
-    moments_kernel<T><<<blocks, threads, 0, s>>>(g, P, f + g.f_off, mask, rho, ux, uy, p);
+cudaError_t moments_impl(const LaunchSet& L, const T* f, double* rho, double* ux, double* uy,
+                         double* p, cudaStream_t s) {
+    moments_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 128), 128, 0, s>>>(
+        L.geoms, L.phys, L.lat0, f, L.mask, rho, ux, uy, p);
     return cudaGetLastError();
 }
 
@@ -181,23 +200,21 @@ cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T*
 
 }  // namespace
 
-cudaError_t launch_init_f32(const Geom& g, float rho_ref, const double* rho, const double* ux,
-                            const double* uy, const uint8_t* mask, float* f, cudaStream_t s) {
-    return init_impl<float>(g, rho_ref, rho, ux, uy, mask, f, s);
+cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
+                            const double* uy, float* f, cudaStream_t s) {
+    return init_impl<float>(L, rho, ux, uy, f, s);
 }
-cudaError_t launch_init_f64(const Geom& g, double rho_ref, const double* rho, const double* ux,
-                            const double* uy, const uint8_t* mask, double* f, cudaStream_t s) {
-    return init_impl<double>(g, rho_ref, rho, ux, uy, mask, f, s);
+cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
+                            const double* uy, double* f, cudaStream_t s) {
+    return init_impl<double>(L, rho, ux, uy, f, s);
 }
-cudaError_t launch_moments_f32(const Geom& g, const Phys<double>& P, const float* f,
-                               const uint8_t* mask, double* rho, double* ux, double* uy,
-                               double* p, cudaStream_t s) {
-    return moments_impl<float>(g, P, f, mask, rho, ux, uy, p, s);
+cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* rho, double* ux,
+                               double* uy, double* p, cudaStream_t s) {
+    return moments_impl<float>(L, f, rho, ux, uy, p, s);
 }
-cudaError_t launch_moments_f64(const Geom& g, const Phys<double>& P, const double* f,
-                               const uint8_t* mask, double* rho, double* ux, double* uy,
-                               double* p, cudaStream_t s) {
-    return moments_impl<double>(g, P, f, mask, rho, ux, uy, p, s);
+cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* rho, double* ux,
+                               double* uy, double* p, cudaStream_t s) {
+    return moments_impl<double>(L, f, rho, ux, uy, p, s);
 }
 cudaError_t launch_mass_f32(const Geom& g, double rho_ref, long long n_fluid, const float* f,
                             const uint8_t* mask, double* partials, double* out, cudaStream_t s) {

@@ -39,6 +39,7 @@ struct Phys {
     T kpsi;               // 2 / (G c^2) of Eq. 13
     T cs2;                // lattice sound speed squared, 1/3
     T s[9];               // diagonal of Lambda, Eq. 2
+    T h[9];               // 1 - s/2, the factor of S in Eq. 3
     T li_e, li_z;         // s_e * 0.75 eps and s_zeta * 0.75 eps (Li's term after (1 - s/2))
 };
 
@@ -64,35 +65,41 @@ __device__ __forceinline__ double psi_bracket_fp64(double rho, double RT, double
     return RT * (num / (om * om * om)) - a * rho - cs2;
 }
 
+// FP32: the quotient and the square root use the fast hardware approximations
+// (about 2 ulp); the state itself is FP32, so they add no visible error.
 __device__ __forceinline__ float psi_of(float rho, const Phys<float>& P, unsigned& flag) {
-    float eta = P.b4 * rho;
-    float om = 1.0f - eta;
-    float num = 1.0f + eta * (1.0f + eta * (1.0f - eta));
-    float q = P.RT * __fdiv_rn(num, om * om * om) - P.a * rho - P.cs2;
+    const float eta = P.b4 * rho;
+    const float om = 1.0f - eta;
+    const float num = fmaf(eta, fmaf(eta, 1.0f - eta, 1.0f), 1.0f);
+    float q = fmaf(P.RT, __fdividef(num, om * om * om), -fmaf(P.a, rho, P.cs2));
     if (fabsf(q) < 0.0078125f * P.cs2)
         q = (float)psi_bracket_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b4,
                                     (double)P.cs2);
     float psi2 = P.kpsi * rho * q;
-    if (!(psi2 >= 0.0f)) {
-        flag |= (psi2 < 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
+    if (!(psi2 >= 0.0f && om > 0.0f)) {
+        flag |= (psi2 < 0.0f && om > 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
         psi2 = 0.0f;
     } else if (psi2 > 3.0e38f) {
         flag |= FLAG_NONFINITE;
     }
-    return __fsqrt_rn(psi2);
+    return psi2 > 0.0f ? psi2 * rsqrtf(psi2) : 0.0f;
 }
 
 __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsigned& flag) {
     double q = psi_bracket_fp64(rho, P.RT, P.a, P.b4, P.cs2);
     double psi2 = P.kpsi * rho * q;
-    if (!(psi2 >= 0.0)) {
-        flag |= (psi2 < 0.0) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
+    const bool dense_ok = (1.0 - P.b4 * rho) > 0.0;
+    if (!(psi2 >= 0.0 && dense_ok)) {
+        flag |= (psi2 < 0.0 && dense_ok) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
         psi2 = 0.0;
     } else if (psi2 > 1.0e300) {
         flag |= FLAG_NONFINITE;
     }
     return sqrt(psi2);
 }
+
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Gather the distribution of node (x, y) after streaming (Eq. 5) from the
 // post-collision array `fin` (pull form): f_a(x) = f*_a(x - e_a), periodic; if
@@ -133,9 +140,17 @@ __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8
     return false;
 }
 
+// Sum of the eight moving populations in a fixed association; the density
+// is f_0 + sum8, and the collision sets f*_0 = drho - sum8(f*) with the same
+// association.
+template <typename T>
+__device__ __forceinline__ T sum8(const T f[9]) {
+    return ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+}
+
 template <typename T>
 __device__ __forceinline__ T sum9(const T f[9]) {
-    return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    return f[0] + sum8(f);
 }
 
 // Collision of one fluid node in moment space (Eq. 3) with m_eq of Eq. 4,
@@ -146,6 +161,8 @@ __device__ __forceinline__ T sum9(const T f[9]) {
 // (Fx, Fy) = -G psi (gx, gy) with g = sum_a w_a psi(x + e_a) e_a (Eq. 7);
 // |F|^2 / psi^2 of Eq. 14 is G^2 |g|^2, and (1 - s/2) / (tau - 1/2) = s, so
 // Li's terms enter m* as +s_e 0.75 eps G^2 |g|^2 and -s_zeta 0.75 eps G^2 |g|^2.
+// For the momentum rows, m_eq = rho v = j + F/2 makes
+// j - s_j (j - rho v) + (1 - s_j/2) F equal to j + F for every s_j.
 template <typename T>
 __device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G2,
                                         const Phys<T>& P) {
@@ -153,51 +170,48 @@ __device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G
     // first moments and velocity, Eq. 6
     const T sx = f[1] - f[3];
     const T sy = f[2] - f[4];
-    const T d58 = f[5] - f[7];
+    const T d57 = f[5] - f[7];
     const T d68 = f[6] - f[8];
-    const T jx = sx + d58 - d68;
-    const T jy = sy + d58 + d68;
+    const T jx = sx + (d57 - d68);
+    const T jy = sy + (d57 + d68);
     const T rvx = jx + half * Fx;       // rho v_x
     const T rvy = jy + half * Fy;
-    const T inv_rho = T(1) / rho;
+    const T inv_rho = recip(rho);
     const T vx = rvx * inv_rho;
     const T vy = rvy * inv_rho;
 
     // m = M f (deviation)
-    const T a14 = (f[1] + f[3]) + (f[2] + f[4]);
-    const T d58p = (f[5] + f[7]) + (f[6] + f[8]);
-    const T m1 = -T(4) * f[0] - a14 + T(2) * d58p;
-    const T m2 = T(4) * f[0] - T(2) * a14 + d58p;
-    const T m4 = -T(2) * sx + d58 - d68;
-    const T m6 = -T(2) * sy + d58 + d68;
-    const T m7 = (f[1] + f[3]) - (f[2] + f[4]);
-    const T m8 = (f[5] + f[7]) - (f[6] + f[8]);
+    const T p13 = f[1] + f[3], p24 = f[2] + f[4];
+    const T p57 = f[5] + f[7], p68 = f[6] + f[8];
+    const T a14 = p13 + p24;
+    const T a58 = p57 + p68;
+    const T m1 = T(2) * a58 - a14 - T(4) * f[0];
+    const T m2 = T(4) * f[0] + a58 - T(2) * a14;
+    const T m4 = (d57 - d68) - T(2) * sx;
+    const T m6 = (d57 + d68) - T(2) * sy;
+    const T m7 = p13 - p24;
+    const T m8 = p57 - p68;
 
     // m_eq of Eq. 4 (deviation form: the rho_ref parts of rho, e, zeta cancel)
     const T ru2 = rvx * vx + rvy * vy;  // rho |v|^2
-    const T meq1 = -T(2) * drho + T(3) * ru2;
+    const T meq1 = T(3) * ru2 - T(2) * drho;
     const T meq2 = drho - T(3) * ru2;
-    const T meq4 = -rvx;
-    const T meq6 = -rvy;
     const T meq7 = rvx * vx - rvy * vy;
     const T meq8 = rvx * vy;
 
-    // source S of Eq. 14 (Eq. 8 plus Li's terms)
-    const T vF = vx * Fx + vy * Fy;
-    const T li = g2G2;
-    // m* = m - s (m - m_eq) + (1 - s/2) S
-    const T ms0 = drho;
-    const T ms1 = m1 - P.s[1] * (m1 - meq1) + (T(1) - half * P.s[1]) * (T(6) * vF) + P.li_e * li;
-    const T ms2 = m2 - P.s[2] * (m2 - meq2) - (T(1) - half * P.s[2]) * (T(6) * vF) - P.li_z * li;
-    const T ms3 = jx - P.s[3] * (jx - rvx) + (T(1) - half * P.s[3]) * Fx;
-    const T ms4 = m4 - P.s[4] * (m4 - meq4) - (T(1) - half * P.s[4]) * Fx;
-    const T ms5 = jy - P.s[5] * (jy - rvy) + (T(1) - half * P.s[5]) * Fy;
-    const T ms6 = m6 - P.s[6] * (m6 - meq6) - (T(1) - half * P.s[6]) * Fy;
-    const T ms7 = m7 - P.s[7] * (m7 - meq7) + (T(1) - half * P.s[7]) * (T(2) * (vx * Fx - vy * Fy));
-    const T ms8 = m8 - P.s[8] * (m8 - meq8) + (T(1) - half * P.s[8]) * (vx * Fy + vy * Fx);
+    // source S of Eq. 14 (Eq. 8 plus Li's terms); m* = m - s (m - m_eq) + (1 - s/2) S
+    const T vF6 = T(6) * (vx * Fx + vy * Fy);
+    const T ms1 = m1 - P.s[1] * (m1 - meq1) + P.h[1] * vF6 + P.li_e * g2G2;
+    const T ms2 = m2 - P.s[2] * (m2 - meq2) - P.h[2] * vF6 - P.li_z * g2G2;
+    const T ms3 = jx + Fx;
+    const T ms4 = m4 - P.s[4] * (m4 + rvx) - P.h[4] * Fx;
+    const T ms5 = jy + Fy;
+    const T ms6 = m6 - P.s[6] * (m6 + rvy) - P.h[6] * Fy;
+    const T ms7 = m7 - P.s[7] * (m7 - meq7) + P.h[7] * (T(2) * (vx * Fx - vy * Fy));
+    const T ms8 = m8 - P.s[8] * (m8 - meq8) + P.h[8] * (vx * Fy + vy * Fx);
 
     // f* = M^-1 m* = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
-    const T a0 = ms0 * T(1.0 / 9.0);
+    const T a0 = drho * T(1.0 / 9.0);
     const T a1 = ms1 * T(1.0 / 36.0);
     const T a2 = ms2 * T(1.0 / 36.0);
     const T a3 = ms3 * T(1.0 / 6.0);
@@ -212,7 +226,6 @@ __device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G
     const T py = a5 - T(2) * a6;
     const T qx = a3 + a4;
     const T qy = a5 + a6;
-    f[0] = a0 - T(4) * a1 + T(4) * a2;
     f[1] = axis + px + a7;
     f[2] = axis + py - a7;
     f[3] = axis - px + a7;
@@ -221,6 +234,13 @@ __device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G
     f[6] = diag - qx + qy - a8;
     f[7] = diag - qx - qy + a8;
     f[8] = diag + qx - qy - a8;
+    // f*_0 = a0 - 4 a1 + 4 a2 in exact arithmetic. Taking it as the remainder
+    // drho - sum8(f*) instead makes the next step's density f*_0 + sum8(f*)
+    // return drho exactly wherever the subtraction is exact (sum8 within a
+    // factor 2 of drho, as in any phase near rest). Otherwise the rounded 1/9
+    // and the identical rounding of every node of a uniform phase would shift
+    // the mass by the same relative amount at every step.
+    f[0] = drho - sum8(f);
 }
 
 // Force sum g = sum_a w_a psi(x + e_a) e_a of Eq. 7 from the nine psi values

@@ -8,11 +8,13 @@
 
 namespace lbm {
 
-// CTA tiles of the step kernel: {TX, TY}. Every tile computes bitwise the same
-// result; they differ only in speed.
-constexpr int kTileCount = 7;
-constexpr int kTiles[kTileCount][2] = {
-    {32, 8}, {64, 4}, {32, 16}, {128, 2}, {64, 8}, {128, 4}, {16, 16},
+// CTA shapes of the step kernel: {TX threads in x, TYT threads in y, RY nodes
+// per thread in y}; the node tile is TX x (TYT * RY). Every shape computes
+// bitwise the same result; they differ only in speed.
+constexpr int kTileCount = 9;
+constexpr int kTiles[kTileCount][3] = {
+    {32, 8, 2}, {32, 8, 1}, {32, 8, 4}, {64, 4, 2}, {64, 4, 4},
+    {32, 4, 4}, {128, 2, 4}, {32, 16, 2}, {64, 8, 2},
 };
 
 template <typename T>
@@ -21,21 +23,29 @@ struct StepArgs;
 cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a, cudaStream_t s);
 cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s);
 
-// Initial state: f_a such that the next pull gathers f_eq(rho, u) at every
-// fluid node. rho/ux/uy are device arrays of nx*ny doubles (ux/uy may be null).
-cudaError_t launch_init_f32(const Geom& g, float rho_ref, const double* rho, const double* ux,
-                            const double* uy, const uint8_t* mask, float* f, cudaStream_t s);
-cudaError_t launch_init_f64(const Geom& g, double rho_ref, const double* rho, const double* ux,
-                            const double* uy, const uint8_t* mask, double* f, cudaStream_t s);
+// Lattices [lat0, lat0 + n_lat) of a context, for the FP64 helper kernels.
+struct LaunchSet {
+    const Geom* geoms;          // device array of every lattice's geometry
+    const Phys<double>* phys;   // device array of every lattice's parameters
+    const uint8_t* mask;        // device mask base (lattice rows at geom.mask_off)
+    int lat0, n_lat;
+    long long max_nodes;        // largest nx*ny among the lattices
+};
 
-// rho, v (Eq. 6), p (Eq. 10) of one lattice into device arrays of nx*ny
-// doubles (any may be null), computed in FP64 from the stored distribution.
-cudaError_t launch_moments_f32(const Geom& g, const Phys<double>& P, const float* f,
-                               const uint8_t* mask, double* rho, double* ux, double* uy,
-                               double* p, cudaStream_t s);
-cudaError_t launch_moments_f64(const Geom& g, const Phys<double>& P, const double* f,
-                               const uint8_t* mask, double* rho, double* ux, double* uy,
-                               double* p, cudaStream_t s);
+// Initial state: f_a such that the next pull gathers f_eq(rho, u) at every
+// fluid node. rho/ux/uy are device arrays indexed by geom.node_off + y*nx + x
+// (ux/uy may be null for u = 0).
+cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
+                            const double* uy, float* f, cudaStream_t s);
+cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
+                            const double* uy, double* f, cudaStream_t s);
+
+// rho, v (Eq. 6), p (Eq. 10) into device arrays indexed like the init inputs
+// (any may be null), computed in FP64 from the stored distribution.
+cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* rho, double* ux,
+                               double* uy, double* p, cudaStream_t s);
+cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* rho, double* ux,
+                               double* uy, double* p, cudaStream_t s);
 
 // Fixed-order FP64 mass of one lattice: sum over fluid nodes of the stored
 // values plus rho_ref * n_fluid. `partials` is scratch of kMassBlocks doubles.

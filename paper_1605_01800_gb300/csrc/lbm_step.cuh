@@ -2,12 +2,14 @@
 // interaction force (Eq. 7), velocity (Eq. 6), MRT collision with Li's source
 // (Eq. 3, 4, 14) and the store of f*, in one pass over HBM.
 //
-// One CTA updates a TX x TY tile of one lattice of the batch. psi is needed on
-// the tile plus a one-node halo; every CTA computes it there itself (pulling
-// the nine populations of each halo node, which neighbouring CTAs also read,
-// so the extra reads are served by L1/L2) and keeps it in shared memory. Each
-// thread keeps its own node's nine pulled populations in registers between the
-// psi phase and the collision, so DRAM sees 9 reads + 9 writes per node.
+// One CTA of TX x TYT threads updates a TX x (TYT * RY) tile of one lattice of
+// the batch; each thread owns RY vertically adjacent nodes of one column. psi
+// is needed on the tile plus a one-node halo: the CTA computes it there itself
+// (pulling the nine populations of each halo node, which neighbouring CTAs
+// also read, so those reads hit L2) and keeps it in shared memory. Each
+// thread's own nodes keep their nine pulled populations in registers between
+// the psi phase and the collision, so DRAM sees 9 reads + 9 writes per node.
+// All RY * 9 loads of a thread are issued before any of them is used.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -25,11 +27,12 @@ struct StepArgs {
     unsigned* status;
 };
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) step_kernel(StepArgs<T> A) {
+template <typename T, int TX, int TYT, int RY>
+__global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
+    constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
-    constexpr int NT = TX * TY;
+    constexpr int NT = TX * TYT;
     constexpr int NH = 2 * SW + 2 * TY;  // halo ring cells
     __shared__ T s_psi[SH * SW];
 
@@ -43,69 +46,125 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(StepArgs<T> A) {
     const T rho_ref = P.rho_ref;
     unsigned flag = 0;
 
-    // ---- own node: pull, density, psi
-    const int lx = threadIdx.x, ly = threadIdx.y;
-    const int x = tile.x0 + lx, y = tile.y0 + ly;
-    const bool own = (x < nx) && (y < ny);
-    const int xw = own ? x : x % nx;
-    const int yw = own ? y : y % ny;
-    T f[9];
-    const bool solid = pull_node<T>(fin, mask, plane, pitch, nx, ny, xw, yw, f);
-    T drho = T(0), rho = T(0), psi = T(-1);
-    if (!solid) {
-        drho = sum9(f);
-        rho = rho_ref + drho;
-        if (!(fabs(rho) < T(1e30))) flag |= FLAG_NONFINITE;
-        psi = psi_of(rho, P, flag);
+    // ---- own nodes: column x, rows y0 .. y0 + RY - 1 (wrapped into the
+    // lattice when the tile overhangs its edge)
+    const int lx = threadIdx.x;
+    const int x = tile.x0 + lx;
+    const int y0 = tile.y0 + threadIdx.y * RY;
+    const int xw = x < nx ? x : x % nx;
+    T f[RY][9];
+    bool solid[RY];
+    if (mask == nullptr) {
+        const int xm = (xw == 0) ? nx - 1 : xw - 1;
+        const int xp = (xw == nx - 1) ? 0 : xw + 1;
+        int row[RY + 2];  // wrapped row offsets of y0 - 1 .. y0 + RY
+#pragma unroll
+        for (int r = 0; r < RY + 2; ++r) {
+            int yy = y0 - 1 + r;
+            yy = (yy < 0) ? yy + ny : yy;
+            yy = (yy < ny) ? yy : yy % ny;
+            row[r] = yy * pitch;
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const int rm = row[r], r0 = row[r + 1], rp = row[r + 2];
+            f[r][0] = fin[r0 + xw];
+            f[r][1] = fin[1 * plane + r0 + xm];
+            f[r][2] = fin[2 * plane + rm + xw];
+            f[r][3] = fin[3 * plane + r0 + xp];
+            f[r][4] = fin[4 * plane + rp + xw];
+            f[r][5] = fin[5 * plane + rm + xm];
+            f[r][6] = fin[6 * plane + rm + xp];
+            f[r][7] = fin[7 * plane + rp + xp];
+            f[r][8] = fin[8 * plane + rp + xm];
+            solid[r] = false;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const int yy = y0 + r;
+            const int yw = yy < ny ? yy : yy % ny;
+            solid[r] = pull_node<T>(fin, mask, plane, pitch, nx, ny, xw, yw, f[r]);
+        }
     }
-    s_psi[(ly + 1) * SW + (lx + 1)] = psi;
 
-    // ---- halo ring: psi only
-    for (int h = threadIdx.y * TX + threadIdx.x; h < NH; h += NT) {
-        int cx, cy;
-        if (h < SW) {
-            cx = h;
-            cy = 0;
-        } else if (h < 2 * SW) {
-            cx = h - SW;
-            cy = SH - 1;
-        } else {
-            const int k = h - 2 * SW;
-            cy = 1 + (k >> 1);
-            cx = (k & 1) ? SW - 1 : 0;
+    // ---- halo ring: psi only (issued before the own nodes' arithmetic)
+    T ph[(NH + NT - 1) / NT];
+    int hc[(NH + NT - 1) / NT];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < (NH + NT - 1) / NT; ++k) {
+        const int h = tid + k * NT;
+        hc[k] = -1;
+        ph[k] = T(-1);
+        if (h < NH) {
+            int cx, cy;
+            if (h < SW) {
+                cx = h;
+                cy = 0;
+            } else if (h < 2 * SW) {
+                cx = h - SW;
+                cy = SH - 1;
+            } else {
+                const int q = h - 2 * SW;
+                cy = 1 + (q >> 1);
+                cx = (q & 1) ? SW - 1 : 0;
+            }
+            hc[k] = cy * SW + cx;
+            const int hx = wrap_index(tile.x0 - 1 + cx, nx);
+            const int hy = wrap_index(tile.y0 - 1 + cy, ny);
+            T fh[9];
+            if (!pull_node<T>(fin, mask, plane, pitch, nx, ny, hx, hy, fh)) {
+                const T rh = rho_ref + sum9(fh);
+                ph[k] = psi_of(rh, P, flag);
+            }
         }
-        const int hx = wrap_index(tile.x0 - 1 + cx, nx);
-        const int hy = wrap_index(tile.y0 - 1 + cy, ny);
-        T fh[9];
-        T ph = T(-1);
-        if (!pull_node<T>(fin, mask, plane, pitch, nx, ny, hx, hy, fh)) {
-            const T rh = rho_ref + sum9(fh);
-            ph = psi_of(rh, P, flag);
-        }
-        s_psi[cy * SW + cx] = ph;
     }
+
+    // ---- own nodes: density and psi
+    T drho[RY], rho[RY], psi[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        drho[r] = T(0);
+        rho[r] = T(0);
+        psi[r] = T(-1);
+        if (!solid[r]) {
+            drho[r] = sum9(f[r]);
+            rho[r] = rho_ref + drho[r];
+            psi[r] = psi_of(rho[r], P, flag);
+        }
+        s_psi[(threadIdx.y * RY + r + 1) * SW + (lx + 1)] = psi[r];
+    }
+#pragma unroll
+    for (int k = 0; k < (NH + NT - 1) / NT; ++k)
+        if (hc[k] >= 0) s_psi[hc[k]] = ph[k];
     __syncthreads();
 
     if (flag) atomicOr(&A.status[tile.lat], flag);
-    if (!own || solid) return;
+    if (x >= nx) return;
 
-    // ---- force, Eq. 7
-    const int c = (ly + 1) * SW + (lx + 1);
-    T gx, gy;
-    force_sum<T>(psi, s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
-                 s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx, gy);
     const T mG = -P.G;
-    const T Fx = mG * psi * gx;
-    const T Fy = mG * psi * gy;
-    const T g2G2 = (P.G * P.G) * (gx * gx + gy * gy);
-
-    // ---- collision, Eq. 3
-    collide<T>(f, rho, drho, Fx, Fy, g2G2, P);
-
-    // ---- store f*
-    T* __restrict__ fo = A.fout + g.f_off + y * pitch + x;
+    const T G2 = P.G * P.G;
+    T* __restrict__ fo = A.fout + g.f_off;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) fo[a * plane] = f[a];
+    for (int r = 0; r < RY; ++r) {
+        const int y = y0 + r;
+        if (y >= ny || solid[r]) continue;
+        // ---- force, Eq. 7
+        const int c = (threadIdx.y * RY + r + 1) * SW + (lx + 1);
+        T gx, gy;
+        force_sum<T>(psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
+                     s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx,
+                     gy);
+        const T Fx = mG * psi[r] * gx;
+        const T Fy = mG * psi[r] * gy;
+        // ---- collision, Eq. 3
+        collide<T>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
+        // ---- store f*
+        T* o = fo + y * pitch + x;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) o[a * plane] = f[r][a];
+    }
 }
 
 }  // namespace lbm

@@ -4,22 +4,24 @@
 
 namespace lbm {
 
-template <int TX, int TY>
+template <int TX, int TYT, int RY>
 static cudaError_t launch_tile(int n_tiles, const StepArgs<float>& a, cudaStream_t s) {
-    step_kernel<float, TX, TY><<<n_tiles, dim3(TX, TY), 0, s>>>(a);
+    step_kernel<float, TX, TYT, RY><<<n_tiles, dim3(TX, TYT), 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     switch (tile_index) {
-    case 0: return launch_tile<32, 8>(n_tiles, a, s);
-    case 1: return launch_tile<64, 4>(n_tiles, a, s);
-    case 2: return launch_tile<32, 16>(n_tiles, a, s);
-    case 3: return launch_tile<128, 2>(n_tiles, a, s);
-    case 4: return launch_tile<64, 8>(n_tiles, a, s);
-    case 5: return launch_tile<128, 4>(n_tiles, a, s);
-    case 6: return launch_tile<16, 16>(n_tiles, a, s);
+    case 0: return launch_tile<32, 8, 2>(n_tiles, a, s);
+    case 1: return launch_tile<32, 8, 1>(n_tiles, a, s);
+    case 2: return launch_tile<32, 8, 4>(n_tiles, a, s);
+    case 3: return launch_tile<64, 4, 2>(n_tiles, a, s);
+    case 4: return launch_tile<64, 4, 4>(n_tiles, a, s);
+    case 5: return launch_tile<32, 4, 4>(n_tiles, a, s);
+    case 6: return launch_tile<128, 2, 4>(n_tiles, a, s);
+    case 7: return launch_tile<32, 16, 2>(n_tiles, a, s);
+    case 8: return launch_tile<64, 8, 2>(n_tiles, a, s);
     default: return cudaErrorInvalidValue;
     }
 }

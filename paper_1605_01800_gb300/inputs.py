@@ -120,7 +120,7 @@ class LatticeSpec:
     s: List[float]
     eps: float
     rho: np.ndarray                       # (ny, nx) initial density, float64
-    rho_ref: float = 0.0                  # deviation reference for FP32 storage
+    rho_ref: float = 0.0                  # deviation reference for FP32 storage (the vapour density)
     solid: Optional[np.ndarray] = None    # (ny, nx) uint8, 1 = solid
     a: float = 1.0
     b: float = 4.0
@@ -138,7 +138,7 @@ def droplet_128() -> List[LatticeSpec]:
     c = coexistence(0.8)
     nx = ny = 128
     rho = tanh_profile(nx, ny, (nx - 1) / 2, (ny - 1) / 2, 25.0, c["rho_g"], c["rho_l"], 2.0)
-    return [LatticeSpec(nx, ny, 0.8 * Tc, relax_rates(1.0), 1.6, rho, rho_ref=c["rho_l"],
+    return [LatticeSpec(nx, ny, 0.8 * Tc, relax_rates(1.0), 1.6, rho, rho_ref=c["rho_g"],
                         meta={"R": 25.0, "rho_l": c["rho_l"], "rho_g": c["rho_g"]})]
 
 
@@ -151,7 +151,7 @@ def coexistence_batch(n: int = 32, nx: int = 256, ny: int = 64, config_id: int =
         rho = slab_profile(nx, ny, nx / 4, 3 * nx / 4, c["rho_l"], c["rho_g"], 5.0)
         noise = uniform_pm1(SEED_BASE + 1000 * config_id + i, nx * ny).reshape(ny, nx)
         rho = rho * (1.0 + 1e-3 * noise)
-        out.append(LatticeSpec(nx, ny, tr * Tc, relax_rates(0.6), 1.86, rho, rho_ref=c["rho_l"],
+        out.append(LatticeSpec(nx, ny, tr * Tc, relax_rates(0.6), 1.86, rho, rho_ref=c["rho_g"],
                                meta={"T_over_Tc": tr, "rho_l": c["rho_l"], "rho_g": c["rho_g"]}))
     return out
 
@@ -171,7 +171,7 @@ def laplace_batch(n: int = 48) -> List[LatticeSpec]:
     for R in laplace_radii(n):
         L = laplace_box(R)
         rho = tanh_profile(L, L, (L - 1) / 2, (L - 1) / 2, R, c["rho_g"], c["rho_l"], 5.0)
-        out.append(LatticeSpec(L, L, 0.6 * Tc, relax_rates(1.0), 1.6, rho, rho_ref=c["rho_l"],
+        out.append(LatticeSpec(L, L, 0.6 * Tc, relax_rates(1.0), 1.6, rho, rho_ref=c["rho_g"],
                                meta={"R": R, "rho_l": c["rho_l"], "rho_g": c["rho_g"]}))
     return out
 
@@ -182,7 +182,7 @@ def cavitation_1024(n: int = 1024, config_id: int = 3) -> List[LatticeSpec]:
     rho0 = 0.98 * c["spinodal_liquid"]
     noise = uniform_pm1(SEED_BASE + 1000 * config_id, n * n).reshape(n, n)
     rho = rho0 * (1.0 + 0.01 * noise)
-    return [LatticeSpec(n, n, 0.6 * Tc, relax_rates(0.8), 1.86, rho, rho_ref=rho0,
+    return [LatticeSpec(n, n, 0.6 * Tc, relax_rates(0.8), 1.86, rho, rho_ref=c["rho_g"],
                         meta={"rho0": rho0, "rho_c": coexistence_table()["rho_c"]})]
 
 
@@ -195,7 +195,7 @@ def collapse(nx: int = 2048, ny: int = 1024, R0: float = 200.0, yc: float = 300.
     solid[0, :] = 1
     solid[ny - 1, :] = 1
     rho[solid == 1] = rho_liq
-    return [LatticeSpec(nx, ny, 0.5 * Tc, relax_rates(0.6), 1.86, rho, rho_ref=rho_liq, solid=solid,
+    return [LatticeSpec(nx, ny, 0.5 * Tc, relax_rates(0.6), 1.86, rho, rho_ref=c["rho_g"], solid=solid,
                         meta={"R0": R0, "yc": yc, "rho_l": rho_liq, "rho_g": c["rho_g"]})]
 
 

@@ -48,4 +48,4 @@ def small_spec(nx, ny, tr=0.7, eps=1.86, tau=0.6, walls=False, seed=7, R=None, s
         solid[0, :] = 1
         solid[ny - 1, :] = 1
     return inputs.LatticeSpec(nx, ny, tr * Tc, inputs.relax_rates(tau), eps, rho,
-                              rho_ref=c["rho_l"], solid=solid)
+                              rho_ref=c["rho_g"], solid=solid)

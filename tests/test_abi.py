@@ -33,9 +33,8 @@ def test_tile_table():
     n = lbm.lbm_tile_count()
     assert n >= 4
     shapes = [lbm.lbm_tile_shape(i) for i in range(n)]
-    assert len(set(shapes)) == n
     for tx, ty in shapes:
-        assert tx % 16 == 0 and 1 <= tx * ty <= 1024
+        assert tx % 32 == 0 and ty >= 1
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_tile_shape(n)
     assert e.value.code == lbm.LBM_EINVAL
