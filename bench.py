@@ -316,7 +316,40 @@ def main():
     fp64_mlups = nodes / (fp64_ms * 1e-3) / 1e6
     b64.close()
 
+    # ---- context: a plain device copy of the same bytes under the same flush
+    src = torch.empty(nodes * 9, dtype=torch.float32, device=dev)
+    dst = torch.empty_like(src)
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(30)]
+    sink = torch.zeros((), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for e0, e1 in cev:
+            flush_l2(flush, sink)
+            e0.record(stream)
+            dst.copy_(src)
+            e1.record(stream)
+    stream.synchronize()
+    copy_ms = statistics.median([a.elapsed_time(b) for a, b in cev])
+    copy_gbs = 2 * src.numel() * 4 / (copy_ms * 1e-3) / 1e9
+    del src, dst
+
+    # ---- context: workloads larger than L2 (one FP32 buffer 75-81 MB, both 151-162 MB)
+    large = {}
+    for name in ("collapse_2048x1024", "laplace_batch"):
+        lspecs = inputs.WORKLOADS[name]()
+        lnodes = sum(s.nodes for s in lspecs)
+        bl = lbm.Batch(lspecs, "fp32_dev", stream=stream)
+        lbm.lbm_set_tile(bl.ctx, best_tile)
+        bl.init()
+        timed_steps(torch, bl.ctx, lbm, stream, flush, 3)
+        lms = statistics.median(timed_steps(torch, bl.ctx, lbm, stream, flush, 20))
+        lgbs = ALG_BYTES_FP32 * lnodes / (lms * 1e-3) / 1e9
+        large[name] = {"nodes": lnodes, "ms_per_step": lms, "MLUPS": lnodes / (lms * 1e-3) / 1e6,
+                       "achieved_gbs": lgbs}
+        bl.close()
+
     peak, peak_kind = measured_peak_hbm()
+    for v in large.values():
+        v["frac"] = v["achieved_gbs"] / peak
     achieved = ALG_BYTES_FP32 * nodes / (ms_per_step * 1e-3) / 1e9
     traffic = profiled_traffic()
 
@@ -335,6 +368,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_node": ALG_BYTES_FP32},
+        "copy_same_bytes": {"achieved_gbs": copy_gbs, "ms": copy_ms, "frac": copy_gbs / peak,
+                            "note": "torch device copy of 9 x 4 B per node, same flush"},
+        "large_workloads": large,
         "fp64_plain": {"value": fp64_mlups, "unit": "MLUPS", "ms_per_step": fp64_ms, "steps": k64,
                        "achieved_gbs": ALG_BYTES_FP64 * nodes / (fp64_ms * 1e-3) / 1e9},
         "l2_resident": {"value": l2_mlups, "unit": "MLUPS",
