@@ -56,6 +56,11 @@ struct HostLattice {
 
 }  // namespace
 
+namespace lbm {
+// Record an error message for lbm_last_error() from another translation unit.
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace lbm
+
 struct lbm_ctx {
     int n = 0;
     int precision = LBM_FP32_DEV;

@@ -37,7 +37,7 @@ EXPORTED = [
     "lbm_step", "lbm_read_moments", "lbm_read_moments_all", "lbm_total_mass", "lbm_status",
     "lbm_clear_status", "lbm_sync", "lbm_state_size", "lbm_save_state", "lbm_load_state",
     "lbm_tile_count", "lbm_tile_shape", "lbm_set_tile", "lbm_autotune", "lbm_info",
-    "lbm_last_error", "lbm_destroy",
+    "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc",
 ]
 
 
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_info.argtypes = [_ctx, ctypes.POINTER(lbm_info_t)]
     lib.lbm_last_error.argtypes = []
     lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_total_mass_fp32_noalloc.argtypes = [_vp, I, I, ctypes.c_double, _vp, _vp, _vp]
     lib.lbm_destroy.argtypes = [_ctx]
     lib.lbm_destroy.restype = None
     for name in EXPORTED:
@@ -249,6 +250,12 @@ def lbm_info(ctx) -> dict:
 
 def lbm_last_error() -> str:
     return load().lbm_last_error().decode()
+
+
+def lbm_total_mass_fp32_noalloc(f_dev_ptr, nx, ny, rho_ref, mask_dev_ptr, mass_dev_ptr, stream_handle=0):
+    """Device-pointer entry point that allocates nothing (see include/lbm.h)."""
+    return _check(load().lbm_total_mass_fp32_noalloc(f_dev_ptr, nx, ny, rho_ref, mask_dev_ptr or None,
+                                                        mass_dev_ptr, stream_handle or None))
 
 
 def lbm_destroy(ctx):
