@@ -249,7 +249,7 @@ def main():
     tile_ms = {}
     for t in range(lbm.lbm_tile_count()):
         lbm.lbm_set_tile(b32.ctx, t)
-        tile_ms[t] = statistics.median(timed_steps(torch, b32.ctx, lbm, stream, flush, 30))
+        tile_ms[t] = statistics.mean(timed_steps(torch, b32.ctx, lbm, stream, flush, 60))
     best_tile = min(tile_ms, key=tile_ms.get)
     lbm.lbm_set_tile(b32.ctx, best_tile)
     b32.init()
@@ -328,7 +328,7 @@ def main():
             dst.copy_(src)
             e1.record(stream)
     stream.synchronize()
-    copy_ms = statistics.median([a.elapsed_time(b) for a, b in cev])
+    copy_ms = statistics.mean([a.elapsed_time(b) for a, b in cev])
     copy_gbs = 2 * src.numel() * 4 / (copy_ms * 1e-3) / 1e9
     del src, dst
 
@@ -341,7 +341,7 @@ def main():
         lbm.lbm_set_tile(bl.ctx, best_tile)
         bl.init()
         timed_steps(torch, bl.ctx, lbm, stream, flush, 3)
-        lms = statistics.median(timed_steps(torch, bl.ctx, lbm, stream, flush, 20))
+        lms = statistics.mean(timed_steps(torch, bl.ctx, lbm, stream, flush, 40))
         lgbs = ALG_BYTES_FP32 * lnodes / (lms * 1e-3) / 1e9
         large[name] = {"nodes": lnodes, "ms_per_step": lms, "MLUPS": lnodes / (lms * 1e-3) / 1e6,
                        "achieved_gbs": lgbs}

@@ -48,6 +48,7 @@ extern "C" {
 #define LBM_ECUDA 3           /* a CUDA runtime call failed */
 #define LBM_EPSI_DOMAIN 4     /* psi^2 of Eq. 13 went negative somewhere and was clamped to 0 */
 #define LBM_ENONFINITE 5      /* a density or psi^2 became NaN or infinite */
+#define LBM_ETIMEOUT 6        /* a bounded device-side wait gave up (the step was not completed) */
 
 /* ---- storage precision (lbm_create*, argument `precision`) --------------- */
 #define LBM_FP32_DEV 0        /* FP32 storage and collision of f_a - w_a rho_ref */
@@ -57,6 +58,7 @@ extern "C" {
 /* ---- sticky per-lattice status bits (lbm_status) ------------------------- */
 #define LBM_FLAG_PSI_CLAMPED 1u
 #define LBM_FLAG_NONFINITE 2u
+#define LBM_FLAG_TIMEOUT 4u
 
 typedef struct lbm_ctx lbm_ctx;
 

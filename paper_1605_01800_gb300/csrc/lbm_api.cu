@@ -52,6 +52,7 @@ struct HostLattice {
     double rho_ref;              // as used by the kernels (FP32-rounded for FP32_DEV)
     bool rho_ref_auto;
     long long n_fluid;
+    long long c_off;             // element offset in the compact checkpoint layout
 };
 
 }  // namespace
@@ -68,6 +69,7 @@ struct lbm_ctx {
     std::vector<HostLattice> lats;
     long long total_nodes = 0, fluid_nodes = 0;
     long long total_elems = 0;   // elements per distribution array
+    long long compact_elems = 0; // elements of the distribution in a checkpoint blob
     long long mask_bytes = 0;
     long long max_nodes = 0;
 
@@ -79,7 +81,13 @@ struct lbm_ctx {
     Phys<double>* d_phys_d = nullptr;
     Tile* d_tiles = nullptr;
     int n_tiles = 0;
+    // TMA variants: tensor maps per variant (box shape) and source buffer,
+    // encoded once and passed to every launch as kernel parameters.
+    static constexpr int kMaxTma = 8;
+    TmaMaps* h_maps[kMaxTma][2] = {};   // host copies passed at launch, by source buffer
+    int tma_grid[kMaxTma] = {};
     int tile_index = 0;
+    bool has_tiny = false;       // a lattice under 4 cells in x or y (see launch_one_step)
     unsigned* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_scalar = nullptr;
@@ -99,9 +107,10 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
 int validate_desc(const lbm_lattice_desc& d, int i) {
     if (d.nx < 1 || d.ny < 1) return fail(LBM_EINVAL, "lattice %d: nx=%d, ny=%d must be >= 1", i, d.nx, d.ny);
-    long long plane = (long long)d.ny * round_up(d.nx, 32);
+    long long plane = (long long)(d.ny + 2 * kGY) * round_up((long long)d.nx + kGX + 2, 32);
     if (9 * plane >= (1ll << 31))
-        return fail(LBM_EINVAL, "lattice %d: %dx%d too large (9*ny*pitch must be < 2^31)", i, d.nx, d.ny);
+        return fail(LBM_EINVAL, "lattice %d: %dx%d too large (9 stored planes must hold < 2^31 elements)", i,
+                    d.nx, d.ny);
     const lbm_eos_params& e = d.eos;
     if (!(std::isfinite(e.a) && std::isfinite(e.b) && std::isfinite(e.R) && std::isfinite(e.T) &&
           std::isfinite(e.G)))
@@ -180,6 +189,8 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->d_phys_f);
     cudaFree(c->d_phys_d);
     cudaFree(c->d_tiles);
+    for (int v = 0; v < lbm_ctx::kMaxTma; ++v)
+        for (int b = 0; b < 2; ++b) delete c->h_maps[v][b];
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
     cudaFree(c->d_scalar);
@@ -187,10 +198,62 @@ void free_ctx(lbm_ctx* c) {
     delete c;
 }
 
+int total_tiles() { return kTileCount + tma_variant_count(); }
+
+void tile_shape(int index, int* tx, int* ty) {
+    if (index < kTileCount) {
+        *tx = kTiles[index][0];
+        *ty = kTiles[index][1] * kTiles[index][2];
+    } else {
+        tma_variant_shape(index - kTileCount, tx, ty);
+    }
+}
+
+// Tensor maps for a TMA variant's box shape (built once per context and
+// variant), and its persistent grid size.
+int build_tma(lbm_ctx* c, int tile_index) {
+    const int v = tile_index - kTileCount;
+    if (v < 0 || v >= lbm_ctx::kMaxTma) return fail(LBM_EINVAL, "no TMA variant %d", tile_index);
+    if (c->n > kTmaMaxLattices)
+        return fail(LBM_EINVAL, "tile %d (TMA) takes batches of at most %d lattices", tile_index, kTmaMaxLattices);
+    if (c->h_maps[v][0] == nullptr) {
+        int tx = 0, ty = 0;
+        tile_shape(tile_index, &tx, &ty);
+        TmaMaps* m0 = new TmaMaps();
+        TmaMaps* m1 = new TmaMaps();
+        memset(m0, 0, sizeof(TmaMaps));
+        memset(m1, 0, sizeof(TmaMaps));
+        for (int l = 0; l < c->n; ++l) {
+            CUtensorMap fm[2];
+            if (!encode_lattice_maps(c->lats[l].geom, tx, ty, (const float*)c->f[0], (const float*)c->f[1],
+                                     c->d_mask, fm, &m0->m[l])) {
+                delete m0;
+                delete m1;
+                return fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed for lattice %d", l);
+            }
+            m0->f[l] = fm[0];
+            m1->f[l] = fm[1];
+            m1->m[l] = m0->m[l];
+        }
+        c->h_maps[v][0] = m0;
+        c->h_maps[v][1] = m1;
+    }
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_sm = tma_blocks_per_sm(v);
+    if (per_sm < 1) return fail(LBM_ECUDA, "TMA step variant %d cannot be resident on this device", tile_index);
+    c->tma_grid[v] = std::min(c->n_tiles, per_sm * sms);
+    return LBM_OK;
+}
+
 // Work-list of one step launch: every tile of every lattice, lattices in
 // creation order, tiles row-major within a lattice.
 int build_tiles(lbm_ctx* c, int tile_index) {
-    const int tx = kTiles[tile_index][0], ty = kTiles[tile_index][1] * kTiles[tile_index][2];
+    if (tile_index >= kTileCount && c->precision == LBM_FP64)
+        return fail(LBM_EINVAL, "tile %d is an FP32 (TMA) variant; this context stores FP64", tile_index);
+    int tx = 0, ty = 0;
+    tile_shape(tile_index, &tx, &ty);
     std::vector<Tile> tiles;
     for (int l = 0; l < c->n; ++l) {
         const Geom& g = c->lats[l].geom;
@@ -214,6 +277,7 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     c->n_tiles = (int)tiles.size();
     c->tile_index = tile_index;
     drop_graphs(c);
+    if (tile_index >= kTileCount) return build_tma(c, tile_index);
     return LBM_OK;
 }
 
@@ -229,15 +293,33 @@ int upload_phys(lbm_ctx* c) {
 }
 
 // One step launch from buffer `src` into buffer 1 - src.
+LaunchSet launch_set(lbm_ctx* c, int lat0, int n_lat) {
+    long long mx = 0;
+    for (int l = lat0; l < lat0 + n_lat; ++l)
+        mx = std::max(mx, (long long)c->lats[l].geom.nx * c->lats[l].geom.ny);
+    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx};
+}
+
 cudaError_t launch_one_step(lbm_ctx* c, int src) {
+    cudaError_t e;
     if (c->precision == LBM_FP64) {
         StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
                            (double*)c->f[1 - src], c->d_mask, c->d_status};
-        return launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
+        e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
+    } else if (c->tile_index >= kTileCount) {
+        const int v = c->tile_index - kTileCount;
+        TmaArgs a{c->d_tiles, c->n_tiles, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status};
+        e = launch_step_tma(v, c->tma_grid[v], a, *c->h_maps[v][src], c->stream);
+    } else {
+        StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
+                          (float*)c->f[1 - src], c->d_mask, c->d_status};
+        e = launch_step_f32(c->tile_index, c->n_tiles, a, c->stream);
     }
-    StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
-                      (float*)c->f[1 - src], c->d_mask, c->d_status};
-    return launch_step_f32(c->tile_index, c->n_tiles, a, c->stream);
+    if (e != cudaSuccess || !c->has_tiny) return e;
+    // lattices under 4 cells wide or high: rewrite their ghost frames
+    const LaunchSet ls = launch_set(c, 0, c->n);
+    return c->precision == LBM_FP64 ? launch_ghost_refresh_f64(ls, (double*)c->f[1 - src], c->stream)
+                                    : launch_ghost_refresh_f32(ls, (float*)c->f[1 - src], c->stream);
 }
 
 bool capturable_stream(cudaStream_t s) {
@@ -272,6 +354,7 @@ int check_lat(lbm_ctx* c, int lat) {
 }
 
 int status_code(unsigned flags) {
+    if (flags & FLAG_TIMEOUT) return fail(LBM_ETIMEOUT, "a device-side wait of the step kernel gave up");
     if (flags & FLAG_NONFINITE) return fail(LBM_ENONFINITE, "a density or psi^2 became non-finite");
     if (flags & FLAG_PSI_CLAMPED)
         return fail(LBM_EPSI_DOMAIN, "psi^2 of Eq. 13 went negative and was clamped to 0");
@@ -307,13 +390,6 @@ int check_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const
         *phys_changed = true;
     }
     return LBM_OK;
-}
-
-LaunchSet launch_set(lbm_ctx* c, int lat0, int n_lat) {
-    long long mx = 0;
-    for (int l = lat0; l < lat0 + n_lat; ++l)
-        mx = std::max(mx, (long long)c->lats[l].geom.nx * c->lats[l].geom.ny);
-    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx};
 }
 
 long long range_nodes(lbm_ctx* c, int lat0, int n_lat) {
@@ -353,6 +429,12 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
                             uy ? c->d_io + 2 * c->total_nodes : nullptr, (float*)c->f[c->cur], c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     c->launches += 1;
+    if (c->has_tiny) {  // lattices under 4 cells: their ghost frames are written separately
+        e = c->precision == LBM_FP64 ? launch_ghost_refresh_f64(ls, (double*)c->f[c->cur], c->stream)
+                                     : launch_ghost_refresh_f32(ls, (float*)c->f[c->cur], c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ghost refresh kernel");
+        c->launches += 1;
+    }
     // the host arrays may be pageable and the staging buffer is reused: wait
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
@@ -413,8 +495,8 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
         Geom& g = L.geom;
         g.nx = desc[i].nx;
         g.ny = desc[i].ny;
-        g.pitch = (int)round_up(g.nx, 32);
-        g.plane = (long long)g.ny * g.pitch;
+        g.pitch = (int)round_up((long long)g.nx + kGX + 2, 32);
+        g.plane = (long long)(g.ny + 2 * kGY) * g.pitch;
         g.f_off = f_off;
         g.node_off = node_off;
         const long long nn = (long long)g.nx * g.ny;
@@ -433,7 +515,10 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
         }
         // keep each lattice's planes 256-byte aligned
         f_off += round_up(9 * g.plane, 64);
+        L.c_off = c->compact_elems;
+        c->compact_elems += round_up(9 * (long long)g.ny * round_up(g.nx, 32), 64);
         node_off += nn;
+        if (g.nx < 4 || g.ny < 4) c->has_tiny = true;
         c->total_nodes += nn;
         c->fluid_nodes += L.n_fluid;
         c->max_nodes = std::max(c->max_nodes, nn);
@@ -475,9 +560,14 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
             const HostLattice& L = c->lats[i];
             if (L.mask.empty()) continue;
             const Geom& g = L.geom;
+            // nodes and their periodic images in the ghost frame
             rows.assign((size_t)g.plane, 0);
-            for (int y = 0; y < g.ny; ++y)
-                memcpy(&rows[(size_t)y * g.pitch], &L.mask[(size_t)y * g.nx], g.nx);
+            for (int y = -kGY; y < g.ny + kGY; ++y)
+                for (int x = -2; x < g.nx + 2; ++x) {
+                    const int xs = (int)(((long long)x % g.nx + g.nx) % g.nx);
+                    const int ys = (int)(((long long)y % g.ny + g.ny) % g.ny);
+                    rows[(size_t)node_index(g, x, y)] = L.mask[(size_t)ys * g.nx + xs];
+                }
             e = cudaMemcpy(c->d_mask + g.mask_off, rows.data(), rows.size(), cudaMemcpyHostToDevice);
         }
     }
@@ -563,7 +653,7 @@ int lbm_step(lbm_ctx* c, int n) {
             int rc = ensure_graph(c, c->cur);
             if (rc) return rc;
             CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            c->launches += kGraphChunk;
+            c->launches += kGraphChunk * (c->has_tiny ? 2 : 1);
             done += kGraphChunk;
             c->steps += kGraphChunk;  // kGraphChunk is even: c->cur unchanged
         }
@@ -571,7 +661,7 @@ int lbm_step(lbm_ctx* c, int n) {
     for (; done < n; ++done) {
         cudaError_t e = launch_one_step(c, c->cur);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        c->launches += 1;
+        c->launches += c->has_tiny ? 2 : 1;
         c->cur ^= 1;
         c->steps += 1;
     }
@@ -653,9 +743,35 @@ int lbm_sync(lbm_ctx* c) {
 int lbm_state_size(lbm_ctx* c, size_t* bytes) {
     if (!c || !bytes) return fail(LBM_EINVAL, "null argument");
     *bytes = 4 * sizeof(uint32_t) + sizeof(long long) + c->n * sizeof(double) +
-             (size_t)c->total_elems * c->elem;
+             (size_t)c->compact_elems * c->elem;
     return LBM_OK;
 }
+
+namespace {
+
+// Copy every lattice's nodes between the device layout (ghost frame, row
+// pitch `pitch`) and the compact checkpoint layout (plane a of lattice l at
+// c_off + a*ny*cpitch, node (x, y) at y*cpitch + x, cpitch = round_up(nx, 32)).
+int copy_compact(lbm_ctx* c, char* host, bool to_host) {
+    for (int l = 0; l < c->n; ++l) {
+        const HostLattice& L = c->lats[l];
+        const Geom& g = L.geom;
+        const size_t cpitch = (size_t)round_up(g.nx, 32);
+        for (int a = 0; a < 9; ++a) {
+            char* h = host + ((size_t)L.c_off + (size_t)a * g.ny * cpitch) * c->elem;
+            char* d = (char*)c->f[c->cur] + ((size_t)g.f_off + (size_t)a * g.plane + node_index(g, 0, 0)) * c->elem;
+            if (to_host)
+                CK(cudaMemcpy2DAsync(h, cpitch * c->elem, d, (size_t)g.pitch * c->elem, (size_t)g.nx * c->elem,
+                                     (size_t)g.ny, cudaMemcpyDeviceToHost, c->stream));
+            else
+                CK(cudaMemcpy2DAsync(d, (size_t)g.pitch * c->elem, h, cpitch * c->elem, (size_t)g.nx * c->elem,
+                                     (size_t)g.ny, cudaMemcpyHostToDevice, c->stream));
+        }
+    }
+    return LBM_OK;
+}
+
+}  // namespace
 
 int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
     size_t need = 0;
@@ -663,7 +779,7 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
     if (rc) return rc;
     if (!buf || bytes < need) return fail(LBM_EINVAL, "state buffer needs %zu bytes, got %zu", need, bytes);
     char* p = (char*)buf;
-    uint32_t hdr[4] = {kStateMagic, (uint32_t)c->precision, (uint32_t)c->n, (uint32_t)c->total_elems};
+    uint32_t hdr[4] = {kStateMagic, (uint32_t)c->precision, (uint32_t)c->n, (uint32_t)c->compact_elems};
     memcpy(p, hdr, sizeof(hdr));
     p += sizeof(hdr);
     memcpy(p, &c->steps, sizeof(long long));
@@ -672,7 +788,9 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
         memcpy(p, &c->lats[l].rho_ref, sizeof(double));
         p += sizeof(double);
     }
-    CK(cudaMemcpyAsync(p, c->f[c->cur], (size_t)c->total_elems * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    memset(p, 0, (size_t)c->compact_elems * c->elem);
+    rc = copy_compact(c, p, true);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -687,7 +805,7 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     memcpy(hdr, p, sizeof(hdr));
     p += sizeof(hdr);
     if (hdr[0] != kStateMagic || hdr[1] != (uint32_t)c->precision || hdr[2] != (uint32_t)c->n ||
-        hdr[3] != (uint32_t)c->total_elems)
+        hdr[3] != (uint32_t)c->compact_elems)
         return fail(LBM_EINVAL, "state blob does not match this context (lattices or precision differ)");
     long long steps;
     memcpy(&steps, p, sizeof(long long));
@@ -700,24 +818,34 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     rc = upload_phys(c);
     if (rc) return rc;
     drop_graphs(c);
-    CK(cudaMemcpyAsync(c->f[c->cur], p, (size_t)c->total_elems * c->elem, cudaMemcpyHostToDevice, c->stream));
+    rc = copy_compact(c, const_cast<char*>(p), false);
+    if (rc) return rc;
+    const LaunchSet ls = launch_set(c, 0, c->n);
+    cudaError_t e = c->precision == LBM_FP64 ? launch_ghost_refresh_f64(ls, (double*)c->f[c->cur], c->stream)
+                                             : launch_ghost_refresh_f32(ls, (float*)c->f[c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ghost refresh kernel");
+    c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));
     c->steps = steps;
     return LBM_OK;
 }
 
-int lbm_tile_count(void) { return kTileCount; }
+int lbm_tile_count(void) { return total_tiles(); }
 
 int lbm_tile_shape(int index, int* tx, int* ty) {
-    if (index < 0 || index >= kTileCount) return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, kTileCount);
-    if (tx) *tx = kTiles[index][0];
-    if (ty) *ty = kTiles[index][1] * kTiles[index][2];
+    if (index < 0 || index >= total_tiles())
+        return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, total_tiles());
+    int a = 0, b = 0;
+    tile_shape(index, &a, &b);
+    if (tx) *tx = a;
+    if (ty) *ty = b;
     return LBM_OK;
 }
 
 int lbm_set_tile(lbm_ctx* c, int index) {
     if (!c) return fail(LBM_EINVAL, "null context");
-    if (index < 0 || index >= kTileCount) return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, kTileCount);
+    if (index < 0 || index >= total_tiles())
+        return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, total_tiles());
     if (index == c->tile_index) return LBM_OK;
     CK(cudaStreamSynchronize(c->stream));
     return build_tiles(c, index);
@@ -752,17 +880,21 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
         cleanup();
         return cuda_fail(e, "autotune set-up");
     }
-    for (int t = 0; t < kTileCount; ++t) {
+    for (int t = 0; t < total_tiles(); ++t) {
+        if (t >= kTileCount && (c->precision == LBM_FP64 || c->n > kTmaMaxLattices)) {
+            if (ms) ms[t] = -1.0;  // FP32-only variant, or too many lattices for it
+            continue;
+        }
         rc = build_tiles(c, t);
         if (rc) break;
         // warm-up launch, then the timed steps
         e = launch_one_step(c, c->cur);
-        c->launches += 1;
+        c->launches += c->has_tiny ? 2 : 1;
         c->cur ^= 1;
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
         for (int k = 0; k < steps && e == cudaSuccess; ++k) {
             e = launch_one_step(c, c->cur);
-            c->launches += 1;
+            c->launches += c->has_tiny ? 2 : 1;
             c->cur ^= 1;
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
@@ -816,8 +948,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->steps = c->steps;
     info->kernel_launches = c->launches;
     info->device_bytes = c->device_bytes;
-    info->tile_x = kTiles[c->tile_index][0];
-    info->tile_y = kTiles[c->tile_index][1] * kTiles[c->tile_index][2];
+    tile_shape(c->tile_index, &info->tile_x, &info->tile_y);
     info->n_tiles = c->n_tiles;
     info->graph_chunk = kGraphChunk;
     return LBM_OK;

@@ -12,8 +12,8 @@ __constant__ int kOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 __constant__ double kWeq[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                                1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
-__device__ __forceinline__ bool is_solid(const uint8_t* mask, int pitch, int x, int y) {
-    return mask != nullptr && mask[y * pitch + x] != 0;
+__device__ __forceinline__ bool is_solid(const uint8_t* mask, const Geom& g, int x, int y) {
+    return mask != nullptr && mask[node_index(g, x, y)] != 0;
 }
 
 // Second-order equilibrium in velocity space, f_eq_a = w_a rho (1 + 3 e.u +
@@ -44,22 +44,24 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % g.nx), y = (int)(i / g.nx);
-        const long long c = (long long)y * g.pitch + x;
-        if (is_solid(mask, g.pitch, x, y)) {
-            for (int b = 0; b < 9; ++b) f[b * g.plane + c] = T(0);
+        T out[9];
+        if (is_solid(mask, g, x, y)) {
+            for (int b = 0; b < 9; ++b) out[b] = T(0);
+            store_node<T>(f, g, x, y, out);
             continue;
         }
         for (int b = 0; b < 9; ++b) {
             const int xt = wrap_index(x + kEx[b], g.nx), yt = wrap_index(y + kEy[b], g.ny);
             double v;
-            if (is_solid(mask, g.pitch, xt, yt)) {
+            if (is_solid(mask, g, xt, yt)) {
                 v = feq(kOpp[b], rho[i], ux ? ux[i] : 0.0, uy ? uy[i] : 0.0);
             } else {
                 const long long j = (long long)yt * g.nx + xt;
                 v = feq(b, rho[j], ux ? ux[j] : 0.0, uy ? uy[j] : 0.0);
             }
-            f[b * g.plane + c] = (T)(v - kWeq[b] * rho_ref);
+            out[b] = (T)(v - kWeq[b] * rho_ref);
         }
+        store_node<T>(f, g, x, y, out);
     }
 }
 
@@ -68,7 +70,7 @@ template <typename T>
 __device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask,
                                             double rho_ref, int x, int y, double out[9]) {
     T tmp[9];
-    if (pull_node<T>(f, mask, (int)g.plane, g.pitch, g.nx, g.ny, x, y, tmp)) return false;
+    if (pull_node<T>(f, mask, (int)g.plane, g.pitch, node_index(g, x, y), tmp)) return false;
     for (int a = 0; a < 9; ++a) out[a] = (double)tmp[a] + kWeq[a] * rho_ref;
     return true;
 }
@@ -111,7 +113,7 @@ __global__ void moments_kernel(const Geom* __restrict__ geoms, const Phys<double
         const double psi = psi_fp64(rho, P);
         double gx = 0.0, gy = 0.0;
         for (int a = 1; a < 9; ++a) {
-            const int xn = wrap_index(x + kEx[a], g.nx), yn = wrap_index(y + kEy[a], g.ny);
+            const int xn = x + kEx[a], yn = y + kEy[a];  // ghost frame covers -1 and n
             double fn[9];
             double pn = psi;  // solid neighbour: the node's own psi
             if (pulled_fp64<T>(g, f, mask, P.rho_ref, xn, yn, fn)) {
@@ -143,8 +145,8 @@ __global__ void mass_partial_kernel(Geom g, const T* __restrict__ f, const uint8
     for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < n;
          i += (long long)kMassBlocks * kMassThreads) {
         const int x = (int)(i % g.nx), y = (int)(i / g.nx);
-        if (is_solid(mask, g.pitch, x, y)) continue;
-        const long long c = (long long)y * g.pitch + x;
+        if (is_solid(mask, g, x, y)) continue;
+        const long long c = node_index(g, x, y);
         double s = 0.0;
         for (int a = 0; a < 9; ++a) s += (double)f[a * g.plane + c];
         acc += s;
@@ -163,6 +165,25 @@ __global__ void mass_final_kernel(const double* __restrict__ partials, double rh
     double s = 0.0;
     for (int b = 0; b < kMassBlocks; ++b) s += partials[b];
     *out = s + rho_ref * (double)n_fluid;
+}
+
+// Rewrite every lattice's ghost frame from the nodes it images (after the
+// node values were written by a copy, e.g. when a checkpoint is loaded).
+template <typename T>
+__global__ void ghost_refresh_kernel(const Geom* __restrict__ geoms, int lat0, T* __restrict__ f_base) {
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    T* f = f_base + g.f_off;
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+        if (!(x < 2 || x >= g.nx - 2 || y < 2 || y >= g.ny - 2)) continue;
+        T v[9];
+        const int c = node_index(g, x, y);
+        for (int a = 0; a < 9; ++a) v[a] = f[a * g.plane + c];
+        store_ghost_images<T>(f, g, x, y, v);
+    }
 }
 
 dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
@@ -198,7 +219,20 @@ cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T*
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t ghost_impl(const LaunchSet& L, T* f, cudaStream_t s) {
+    ghost_refresh_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(L.geoms, L.lat0, f);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_ghost_refresh_f32(const LaunchSet& L, float* f, cudaStream_t s) {
+    return ghost_impl<float>(L, f, s);
+}
+cudaError_t launch_ghost_refresh_f64(const LaunchSet& L, double* f, cudaStream_t s) {
+    return ghost_impl<double>(L, f, s);
+}
 
 cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
                             const double* uy, float* f, cudaStream_t s) {

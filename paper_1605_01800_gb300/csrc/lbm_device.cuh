@@ -3,9 +3,15 @@
 //
 // Layout in HBM (one array per ping-pong buffer, all lattices of a batch):
 //   lattice L owns 9 planes starting at element geom[L].f_off; plane a holds
-//   f_a (or its deviation f_a - w_a rho_ref) at element a*plane + y*pitch + x,
-//   pitch = round_up(nx, 32) so that every row starts on a 128-byte boundary.
-//   The wall mask uses the same y*pitch + x indexing at geom[L].mask_off.
+//   f_a (or its deviation f_a - w_a rho_ref) at element a*plane + idx(x, y),
+//   idx(x, y) = (y + kGY) * pitch + x + kGX. Around the nx x ny nodes each
+//   plane keeps a two-cell ghost frame (x in {-2, -1, nx, nx + 1}, y in
+//   {-2, -1, ny, ny + 1}) holding the periodic images of the edge nodes; the
+//   kernel that writes a node also writes its images. Streaming therefore
+//   needs no wrap-around arithmetic, and any tile plus a two-cell halo is a
+//   plain rectangle of memory. kGX = 32 keeps node x = 0 (and every row's
+//   first node) on a 128-byte boundary; pitch = round_up(nx + 34, 32).
+//   The wall mask uses the same idx() (one byte per cell, ghosts included).
 //
 // Velocity numbering (weights of Eq. 7: axis 1-4, diagonal 5-8):
 //   e0 (0,0) e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1)
@@ -20,15 +26,23 @@ namespace lbm {
 
 constexpr unsigned FLAG_PSI_CLAMPED = 1u;
 constexpr unsigned FLAG_NONFINITE = 2u;
+constexpr unsigned FLAG_TIMEOUT = 4u;   // a bounded device-side wait gave up
+
+constexpr int kGX = 32;  // stored column of node x = 0
+constexpr int kGY = 2;   // stored row of node y = 0
 
 // Geometry of one lattice of the batch.
 struct Geom {
     int nx, ny, pitch, has_mask;
     long long f_off;     // element offset of plane 0 in the distribution arrays
-    long long plane;     // elements per plane (ny * pitch)
-    long long mask_off;  // byte offset of this lattice's mask rows
+    long long plane;     // elements per plane ((ny + 2 kGY) * pitch)
+    long long mask_off;  // byte offset of this lattice's mask plane
     long long node_off;  // offset of this lattice in concatenated host arrays
 };
+
+__host__ __device__ __forceinline__ int node_index(const Geom& g, int x, int y) {
+    return (y + kGY) * g.pitch + x + kGX;
+}
 
 // Physical parameters of one lattice in the arithmetic type T.
 template <typename T>
@@ -51,6 +65,14 @@ struct Tile {
 __device__ __forceinline__ int wrap_index(int i, int n) {
     int r = i % n;
     return r < 0 ? r + n : r;
+}
+
+// Wrap an index that is at most one period outside [0, n) without a division;
+// only lattices narrower than the tile need the general wrap_index.
+__device__ __forceinline__ int wrap_near(int i, int n) {
+    i = (i < 0) ? i + n : i;
+    i = (i >= n) ? i - n : i;
+    return (i >= 0 && i < n) ? i : wrap_index(i, n);
 }
 
 // psi of Eq. 13 with the CS pressure of Eq. 15, written as
@@ -101,43 +123,93 @@ __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsi
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// Gather the distribution of node (x, y) after streaming (Eq. 5) from the
-// post-collision array `fin` (pull form): f_a(x) = f*_a(x - e_a), periodic; if
-// x - e_a is solid the link is reflected: f_a(x) = f*_abar(x). Coordinates are
-// already wrapped into the lattice. Returns true if (x, y) itself is solid
-// (then f is not filled).
+// Gather the distribution of the cell at stored index c after streaming
+// (Eq. 5) from the post-collision array `fin` (pull form):
+// f_a(x) = f*_a(x - e_a); periodic images come from the ghost frame, so c may
+// be any cell with x in [-1, nx] and y in [-1, ny]. With a wall mask, a link
+// whose source is solid is reflected: f_a(x) = f*_abar(x). Returns true if
+// the cell itself is solid (then f is not filled).
 template <typename T>
 __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8_t* __restrict__ mask,
-                                          int plane, int pitch, int nx, int ny, int x, int y, T f[9]) {
-    const int xm = (x == 0) ? nx - 1 : x - 1;
-    const int xp = (x == nx - 1) ? 0 : x + 1;
-    const int r0 = y * pitch;
-    const int rm = ((y == 0) ? ny - 1 : y - 1) * pitch;
-    const int rp = ((y == ny - 1) ? 0 : y + 1) * pitch;
+                                          int plane, int pitch, int c, T f[9]) {
     if (mask != nullptr) {
-        if (mask[r0 + x]) return true;
-        const int c = r0 + x;
+        if (mask[c]) return true;
         f[0] = fin[c];
-        f[1] = mask[r0 + xm] ? fin[3 * plane + c] : fin[1 * plane + r0 + xm];
-        f[2] = mask[rm + x]  ? fin[4 * plane + c] : fin[2 * plane + rm + x];
-        f[3] = mask[r0 + xp] ? fin[1 * plane + c] : fin[3 * plane + r0 + xp];
-        f[4] = mask[rp + x]  ? fin[2 * plane + c] : fin[4 * plane + rp + x];
-        f[5] = mask[rm + xm] ? fin[7 * plane + c] : fin[5 * plane + rm + xm];
-        f[6] = mask[rm + xp] ? fin[8 * plane + c] : fin[6 * plane + rm + xp];
-        f[7] = mask[rp + xp] ? fin[5 * plane + c] : fin[7 * plane + rp + xp];
-        f[8] = mask[rp + xm] ? fin[6 * plane + c] : fin[8 * plane + rp + xm];
+        f[1] = mask[c - 1]         ? fin[3 * plane + c] : fin[1 * plane + c - 1];
+        f[2] = mask[c - pitch]     ? fin[4 * plane + c] : fin[2 * plane + c - pitch];
+        f[3] = mask[c + 1]         ? fin[1 * plane + c] : fin[3 * plane + c + 1];
+        f[4] = mask[c + pitch]     ? fin[2 * plane + c] : fin[4 * plane + c + pitch];
+        f[5] = mask[c - pitch - 1] ? fin[7 * plane + c] : fin[5 * plane + c - pitch - 1];
+        f[6] = mask[c - pitch + 1] ? fin[8 * plane + c] : fin[6 * plane + c - pitch + 1];
+        f[7] = mask[c + pitch + 1] ? fin[5 * plane + c] : fin[7 * plane + c + pitch + 1];
+        f[8] = mask[c + pitch - 1] ? fin[6 * plane + c] : fin[8 * plane + c + pitch - 1];
         return false;
     }
-    f[0] = fin[r0 + x];
-    f[1] = fin[1 * plane + r0 + xm];
-    f[2] = fin[2 * plane + rm + x];
-    f[3] = fin[3 * plane + r0 + xp];
-    f[4] = fin[4 * plane + rp + x];
-    f[5] = fin[5 * plane + rm + xm];
-    f[6] = fin[6 * plane + rm + xp];
-    f[7] = fin[7 * plane + rp + xp];
-    f[8] = fin[8 * plane + rp + xm];
+    f[0] = fin[c];
+    f[1] = fin[1 * plane + c - 1];
+    f[2] = fin[2 * plane + c - pitch];
+    f[3] = fin[3 * plane + c + 1];
+    f[4] = fin[4 * plane + c + pitch];
+    f[5] = fin[5 * plane + c - pitch - 1];
+    f[6] = fin[6 * plane + c - pitch + 1];
+    f[7] = fin[7 * plane + c + pitch + 1];
+    f[8] = fin[8 * plane + c + pitch - 1];
     return false;
+}
+
+// Write the nine values of node (x, y) (0 <= x < nx, 0 <= y < ny) and, for a
+// node within two cells of an edge, every ghost cell whose periodic image it
+// is. `base` is plane 0 of the lattice.
+template <typename T>
+__device__ __forceinline__ void store_ghost_images(T* __restrict__ base, const Geom& g, int x, int y,
+                                                const T v[9]) {
+    int xs[5], ys[5];
+    int nxs = 0, nys = 0;
+    xs[nxs++] = x;
+    ys[nys++] = y;
+    const int gxs[4] = {-2, -1, g.nx, g.nx + 1};
+    const int gys[4] = {-2, -1, g.ny, g.ny + 1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (wrap_index(gxs[k], g.nx) == x) xs[nxs++] = gxs[k];
+        if (wrap_index(gys[k], g.ny) == y) ys[nys++] = gys[k];
+    }
+    for (int j = 0; j < nys; ++j)
+        for (int i = 0; i < nxs; ++i) {
+            if (i == 0 && j == 0) continue;
+            const int c = node_index(g, xs[i], ys[j]);
+            for (int a = 0; a < 9; ++a) base[a * g.plane + c] = v[a];
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, int x, int y,
+                                           const T v[9]) {
+    const int c = node_index(g, x, y);
+    const int plane = (int)g.plane;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) base[a * plane + c] = v[a];
+    const bool ex = x < 2 || x >= g.nx - 2;
+    const bool ey = y < 2 || y >= g.ny - 2;
+    if (!(ex || ey)) return;
+    // lattices under 4 cells in x or y can have several images per node;
+    // their frames are rewritten by ghost_refresh_kernel after each step
+    if (g.nx < 4 || g.ny < 4) return;
+    // one image per direction at most: x +- nx and y +- ny (offsets in cells)
+    const int dx = !ex ? 0 : (x < 2 ? g.nx : -g.nx);
+    const int dy = !ey ? 0 : (y < 2 ? g.ny : -g.ny) * g.pitch;
+    if (dx != 0) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) base[a * plane + c + dx] = v[a];
+    }
+    if (dy != 0) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) base[a * plane + c + dy] = v[a];
+        if (dx != 0) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) base[a * plane + c + dx + dy] = v[a];
+        }
+    }
 }
 
 // Sum of the eight moving populations in a fixed association; the density
@@ -244,19 +316,21 @@ __device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G
 }
 
 // Force sum g = sum_a w_a psi(x + e_a) e_a of Eq. 7 from the nine psi values
-// of a 3x3 neighbourhood (p[dy+1][dx+1]); a negative entry marks a solid
-// neighbour, which takes the centre node's psi.
+// of a 3x3 neighbourhood; on lattices with walls a negative entry marks a
+// solid neighbour, which takes the centre node's psi.
 template <typename T>
-__device__ __forceinline__ void force_sum(T c, T pe, T pn, T pw, T ps, T pne, T pnw, T psw,
-                                          T pse, T& gx, T& gy) {
-    pe = pe < T(0) ? c : pe;
-    pn = pn < T(0) ? c : pn;
-    pw = pw < T(0) ? c : pw;
-    ps = ps < T(0) ? c : ps;
-    pne = pne < T(0) ? c : pne;
-    pnw = pnw < T(0) ? c : pnw;
-    psw = psw < T(0) ? c : psw;
-    pse = pse < T(0) ? c : pse;
+__device__ __forceinline__ void force_sum(bool walls, T c, T pe, T pn, T pw, T ps, T pne, T pnw,
+                                          T psw, T pse, T& gx, T& gy) {
+    if (walls) {
+        pe = pe < T(0) ? c : pe;
+        pn = pn < T(0) ? c : pn;
+        pw = pw < T(0) ? c : pw;
+        ps = ps < T(0) ? c : ps;
+        pne = pne < T(0) ? c : pne;
+        pnw = pnw < T(0) ? c : pnw;
+        psw = psw < T(0) ? c : psw;
+        pse = pse < T(0) ? c : pse;
+    }
     const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0);
     gx = third * (pe - pw) + twelfth * ((pne - pnw) + (pse - psw));
     gy = third * (pn - ps) + twelfth * ((pne + pnw) - (psw + pse));

@@ -2,6 +2,7 @@
 // family, so that the library builds in parallel).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -13,12 +14,38 @@ namespace lbm {
 // bitwise the same result; they differ only in speed.
 constexpr int kTileCount = 9;
 constexpr int kTiles[kTileCount][3] = {
-    {32, 8, 2}, {32, 8, 1}, {32, 8, 4}, {64, 4, 2}, {64, 4, 4},
-    {32, 4, 4}, {128, 2, 4}, {32, 16, 2}, {64, 8, 2},
+    {32, 8, 2}, {32, 8, 1}, {64, 4, 2}, {64, 4, 1}, {32, 16, 1},
+    {32, 4, 2}, {32, 8, 4}, {64, 8, 1}, {128, 2, 2},
 };
 
 template <typename T>
 struct StepArgs;
+
+// TMA-staged persistent FP32 variants (lbm_step_tma.cu); tile indices
+// kTileCount .. kTileCount + tma_variant_count() - 1 of the public tile list.
+struct TmaArgs {
+    const Tile* tiles;
+    int n_tiles;
+    const Geom* geom;
+    const Phys<float>* phys;
+    float* fout;               // buffer written this step (whole array)
+    unsigned* status;
+};
+// Tensor maps travel as __grid_constant__ kernel parameters: per lattice the
+// map of the buffer read this step and the map of its wall mask.
+constexpr int kTmaMaxLattices = 64;
+struct TmaMaps {
+    CUtensorMap f[kTmaMaxLattices];
+    CUtensorMap m[kTmaMaxLattices];
+};
+int tma_variant_count();
+void tma_variant_shape(int v, int* tx, int* ty);
+int tma_blocks_per_sm(int v);
+cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps, cudaStream_t s);
+// Tensor maps of lattice g in both buffers (fmaps2[0..1]) and of its mask
+// (mmap; zeroed when the lattice has no mask), boxes for a tx x ty tile.
+bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const float* buf1,
+                         const uint8_t* mask_base, CUtensorMap* fmaps2, CUtensorMap* mmap);
 
 cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a, cudaStream_t s);
 cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s);
@@ -46,6 +73,10 @@ cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* rho, 
                                double* uy, double* p, cudaStream_t s);
 cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s);
+
+// Rewrite the ghost frames of lattices [lat0, lat0 + n_lat) from their nodes.
+cudaError_t launch_ghost_refresh_f32(const LaunchSet& L, float* f, cudaStream_t s);
+cudaError_t launch_ghost_refresh_f64(const LaunchSet& L, double* f, cudaStream_t s);
 
 // Fixed-order FP64 mass of one lattice: sum over fluid nodes of the stored
 // values plus rho_ref * n_fluid. `partials` is scratch of kMassBlocks doubles.

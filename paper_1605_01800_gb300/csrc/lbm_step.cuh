@@ -8,8 +8,10 @@
 // (pulling the nine populations of each halo node, which neighbouring CTAs
 // also read, so those reads hit L2) and keeps it in shared memory. Each
 // thread's own nodes keep their nine pulled populations in registers between
-// the psi phase and the collision, so DRAM sees 9 reads + 9 writes per node.
-// All RY * 9 loads of a thread are issued before any of them is used.
+// the psi phase and the collision, so DRAM sees 9 reads + 9 writes per node
+// (plus the ghost images of edge nodes). The ghost frame of the layout makes
+// every pull a fixed offset. All RY * 9 loads of a thread are issued before
+// any of them is used.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -27,8 +29,11 @@ struct StepArgs {
     unsigned* status;
 };
 
+// Register cap for the FP32 kernel with up to two nodes per thread: 64 per
+// thread, so that 1024 threads per SM are resident.
 template <typename T, int TX, int TYT, int RY>
-__global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
+__global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 && RY <= 2) ? 1024 / (TX * TYT) : 1)
+    step_kernel(StepArgs<T> A) {
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
@@ -38,7 +43,10 @@ __global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
 
     const Tile tile = A.tiles[blockIdx.x];
     const Geom g = A.geom[tile.lat];
-    const Phys<T>& P = A.phys[tile.lat];
+    // restrict: the stores to fout cannot alias the parameters, so they need
+    // not be reloaded after every store
+    const Phys<T>* __restrict__ Pp = A.phys + tile.lat;
+    const Phys<T>& P = *Pp;
     const T* __restrict__ fin = A.fin + g.f_off;
     const uint8_t* __restrict__ mask = g.has_mask ? A.mask + g.mask_off : nullptr;
     const int plane = (int)g.plane;
@@ -46,46 +54,19 @@ __global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
     const T rho_ref = P.rho_ref;
     unsigned flag = 0;
 
-    // ---- own nodes: column x, rows y0 .. y0 + RY - 1 (wrapped into the
-    // lattice when the tile overhangs its edge)
+    // ---- own nodes: column x, rows y0 .. y0 + RY - 1. Cells past the last
+    // node (a tile overhanging the lattice) are pulled only up to x = nx and
+    // y = ny, the ghost images the last nodes' forces need.
     const int lx = threadIdx.x;
     const int x = tile.x0 + lx;
     const int y0 = tile.y0 + threadIdx.y * RY;
-    const int xw = x < nx ? x : x % nx;
     T f[RY][9];
-    bool solid[RY];
-    if (mask == nullptr) {
-        const int xm = (xw == 0) ? nx - 1 : xw - 1;
-        const int xp = (xw == nx - 1) ? 0 : xw + 1;
-        int row[RY + 2];  // wrapped row offsets of y0 - 1 .. y0 + RY
+    bool live[RY];
 #pragma unroll
-        for (int r = 0; r < RY + 2; ++r) {
-            int yy = y0 - 1 + r;
-            yy = (yy < 0) ? yy + ny : yy;
-            yy = (yy < ny) ? yy : yy % ny;
-            row[r] = yy * pitch;
-        }
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int rm = row[r], r0 = row[r + 1], rp = row[r + 2];
-            f[r][0] = fin[r0 + xw];
-            f[r][1] = fin[1 * plane + r0 + xm];
-            f[r][2] = fin[2 * plane + rm + xw];
-            f[r][3] = fin[3 * plane + r0 + xp];
-            f[r][4] = fin[4 * plane + rp + xw];
-            f[r][5] = fin[5 * plane + rm + xm];
-            f[r][6] = fin[6 * plane + rm + xp];
-            f[r][7] = fin[7 * plane + rp + xp];
-            f[r][8] = fin[8 * plane + rp + xm];
-            solid[r] = false;
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int yy = y0 + r;
-            const int yw = yy < ny ? yy : yy % ny;
-            solid[r] = pull_node<T>(fin, mask, plane, pitch, nx, ny, xw, yw, f[r]);
-        }
+    for (int r = 0; r < RY; ++r) {
+        const int y = y0 + r;
+        live[r] = (x <= nx) && (y <= ny);
+        if (live[r]) live[r] = !pull_node<T>(fin, mask, plane, pitch, node_index(g, x, y), f[r]);
     }
 
     // ---- halo ring: psi only (issued before the own nodes' arithmetic)
@@ -111,10 +92,10 @@ __global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
                 cx = (q & 1) ? SW - 1 : 0;
             }
             hc[k] = cy * SW + cx;
-            const int hx = wrap_index(tile.x0 - 1 + cx, nx);
-            const int hy = wrap_index(tile.y0 - 1 + cy, ny);
+            const int hx = tile.x0 - 1 + cx, hy = tile.y0 - 1 + cy;
             T fh[9];
-            if (!pull_node<T>(fin, mask, plane, pitch, nx, ny, hx, hy, fh)) {
+            if (hx <= nx && hy <= ny &&
+                !pull_node<T>(fin, mask, plane, pitch, node_index(g, hx, hy), fh)) {
                 const T rh = rho_ref + sum9(fh);
                 ph[k] = psi_of(rh, P, flag);
             }
@@ -128,7 +109,7 @@ __global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
         drho[r] = T(0);
         rho[r] = T(0);
         psi[r] = T(-1);
-        if (!solid[r]) {
+        if (live[r]) {
             drho[r] = sum9(f[r]);
             rho[r] = rho_ref + drho[r];
             psi[r] = psi_of(rho[r], P, flag);
@@ -149,21 +130,19 @@ __global__ void __launch_bounds__(TX * TYT) step_kernel(StepArgs<T> A) {
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int y = y0 + r;
-        if (y >= ny || solid[r]) continue;
+        if (y >= ny || !live[r]) continue;
         // ---- force, Eq. 7
         const int c = (threadIdx.y * RY + r + 1) * SW + (lx + 1);
         T gx, gy;
-        force_sum<T>(psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
+        force_sum<T>(mask != nullptr, psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
                      s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx,
                      gy);
         const T Fx = mG * psi[r] * gx;
         const T Fy = mG * psi[r] * gy;
         // ---- collision, Eq. 3
         collide<T>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
-        // ---- store f*
-        T* o = fo + y * pitch + x;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) o[a * plane] = f[r][a];
+        // ---- store f* (and its ghost images near an edge)
+        store_node<T>(fo, g, x, y, f[r]);
     }
 }
 

@@ -15,13 +15,13 @@ cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& 
     switch (tile_index) {
     case 0: return launch_tile<32, 8, 2>(n_tiles, a, s);
     case 1: return launch_tile<32, 8, 1>(n_tiles, a, s);
-    case 2: return launch_tile<32, 8, 4>(n_tiles, a, s);
-    case 3: return launch_tile<64, 4, 2>(n_tiles, a, s);
-    case 4: return launch_tile<64, 4, 4>(n_tiles, a, s);
-    case 5: return launch_tile<32, 4, 4>(n_tiles, a, s);
-    case 6: return launch_tile<128, 2, 4>(n_tiles, a, s);
-    case 7: return launch_tile<32, 16, 2>(n_tiles, a, s);
-    case 8: return launch_tile<64, 8, 2>(n_tiles, a, s);
+    case 2: return launch_tile<64, 4, 2>(n_tiles, a, s);
+    case 3: return launch_tile<64, 4, 1>(n_tiles, a, s);
+    case 4: return launch_tile<32, 16, 1>(n_tiles, a, s);
+    case 5: return launch_tile<32, 4, 2>(n_tiles, a, s);
+    case 6: return launch_tile<32, 8, 4>(n_tiles, a, s);
+    case 7: return launch_tile<64, 8, 1>(n_tiles, a, s);
+    case 8: return launch_tile<128, 2, 2>(n_tiles, a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,404 @@
+// TMA-staged, persistent variant of the fused FP32 step kernel.
+//
+// Same arithmetic per node as step_kernel (lbm_step.cuh), different data
+// movement. The tensor maps are __grid_constant__ kernel parameters (per
+// lattice: the buffer read this step and the wall mask), so batches of up to
+// kTmaMaxLattices lattices can use these variants. Each CTA owns a strided subset of the tile work-list. For a tile
+// it needs, per population a, the post-collision values of the tile plus a
+// two-cell frame: one 3-D TMA box load per population ({TX+8, TY+4, 1} at
+// stored (x0 + kGX - 4, y0 + kGY - 2, a); the x origin is 16-byte aligned) and,
+// for lattices with walls, one 2-D box of the wall mask. The ghost frame of
+// the layout makes every box a plain rectangle, also at the lattice edges.
+// Loads for the next S - 1 tiles are in flight (an mbarrier per stage) while
+// the current tile is collided, so the SM has DRAM traffic outstanding
+// without holding it in registers. Pulls become shared-memory reads at fixed
+// offsets; the CTA's threads store f* to HBM directly (coalesced rows).
+//
+// Every wait on an mbarrier is bounded (about a second of clock cycles). If a
+// stage never completes the CTA records FLAG_TIMEOUT for the lattice, waits
+// (bounded again) for the stages it has in flight, and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "lbm_launch.h"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Spin on the phase with a clock limit; false if it never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr long long kWaitLimit = 2000000000LL;  // clock cycles, about one second
+
+// e_a and the opposite population, as compile-time tables for the gathers
+__device__ __forceinline__ constexpr int ex_of(int a) {
+    return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int ey_of(int a) {
+    return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int opp_of(int a) {
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 5 + 2) & 3) + 5);
+}
+
+}  // namespace
+
+template <int TX, int TY>
+struct TmaBox {
+    static constexpr int BW = TX + 8;     // stored x in [x0 - 4, x0 + TX + 4)
+    static constexpr int BH = TY + 4;     // stored y in [y0 - 2, y0 + TY + 2)
+    static constexpr int BOX = BW * BH;   // floats of one population's box
+    static constexpr int BOX_BYTES = BOX * 4;
+    static constexpr int MW = TX + 32;    // mask box: x in [x0 - 16, x0 + TX + 16)
+    static constexpr int MASK_BYTES = MW * BH;
+    static constexpr int STAGE_BYTES = ((9 * BOX_BYTES + MASK_BYTES) + 127) / 128 * 128;
+    static_assert(BOX_BYTES % 128 == 0, "population boxes must stay 128-byte aligned");
+};
+
+template <int TX, int TY, int RY, int S>
+__global__ void __launch_bounds__(TX*(TY / RY), 1)
+    step_tma_kernel(const TmaArgs A, const __grid_constant__ TmaMaps M) {
+    using B = TmaBox<TX, TY>;
+    constexpr int TYT = TY / RY;
+    constexpr int NT = TX * TYT;
+    constexpr int SW = TX + 2;
+    constexpr int SH = TY + 2;
+    constexpr int NH = 2 * SW + 2 * TY;
+    constexpr int NHT = (NH + NT - 1) / NT;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float* s_psi = reinterpret_cast<float*>(smem + S * B::STAGE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16);
+
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // thread 0: arm stage s for tile t and issue its box loads
+    auto issue = [&](int t, int s) {
+        const Tile tl = A.tiles[t];
+        const int has_mask = A.geom[tl.lat].has_mask;
+        unsigned char* st = smem + s * B::STAGE_BYTES;
+        mbar_arrive_expect_tx(&bars[s], 9 * B::BOX_BYTES + (has_mask ? B::MASK_BYTES : 0));
+        const CUtensorMap* fm = &M.f[tl.lat];
+        const int bx = tl.x0 + kGX - 4, by = tl.y0 + kGY - 2;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) tma_load_3d(st + a * B::BOX_BYTES, fm, bx, by, a, &bars[s]);
+        if (has_mask) tma_load_2d(st + 9 * B::BOX_BYTES, &M.m[tl.lat], tl.x0 + kGX - 16, by, &bars[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            const int t = blockIdx.x + s * gridDim.x;
+            if (t < A.n_tiles) issue(t, s);
+        }
+    }
+
+    int k = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x, ++k) {
+        const int s = k % S;
+        const uint32_t parity = (uint32_t)((k / S) & 1);
+        const bool ok = mbar_wait_bounded(&bars[s], parity, kWaitLimit);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            if (tid == 0) atomicOr(&A.status[A.tiles[t].lat], FLAG_TIMEOUT);
+            break;
+        }
+        const Tile tl = A.tiles[t];
+        const Geom g = A.geom[tl.lat];
+        const Phys<float>* __restrict__ Pp = A.phys + tl.lat;
+        const Phys<float>& P = *Pp;
+        const float* __restrict__ st = reinterpret_cast<const float*>(smem + s * B::STAGE_BYTES);
+        const uint8_t* __restrict__ ms =
+            g.has_mask ? reinterpret_cast<const uint8_t*>(smem + s * B::STAGE_BYTES + 9 * B::BOX_BYTES) : nullptr;
+        const float rho_ref = P.rho_ref;
+        unsigned flag = 0;
+
+        // pulled populations of the cell at tile-local (lx, ly), lx in [-1, TX],
+        // ly in [-1, TY]; false if the cell is solid
+        auto gather = [&](int lx, int ly, float f[9]) -> bool {
+            const int o = (ly + 2) * B::BW + (lx + 4);  // the cell itself in every box
+            if (ms != nullptr) {
+                const int mo = (ly + 2) * B::MW + (lx + 16);
+                if (ms[mo]) return false;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int d = ey_of(a) * B::BW + ex_of(a);
+                    const int md = ey_of(a) * B::MW + ex_of(a);
+                    f[a] = (a != 0 && ms[mo - md]) ? st[opp_of(a) * B::BOX + o] : st[a * B::BOX + o - d];
+                }
+                return true;
+            }
+#pragma unroll
+            for (int a = 0; a < 9; ++a) f[a] = st[a * B::BOX + o - (ey_of(a) * B::BW + ex_of(a))];
+            return true;
+        };
+
+        // ---- own nodes
+        float f[RY][9];
+        bool live[RY];
+        float drho[RY], rho[RY], psi[RY];
+        const int lx = threadIdx.x;
+        const int x = tl.x0 + lx;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const int ly = threadIdx.y * RY + r;
+            const int y = tl.y0 + ly;
+            live[r] = (x <= g.nx) && (y <= g.ny);
+            if (live[r]) live[r] = gather(lx, ly, f[r]);
+            drho[r] = 0.0f;
+            rho[r] = 0.0f;
+            psi[r] = -1.0f;
+            if (live[r]) {
+                drho[r] = sum9(f[r]);
+                rho[r] = rho_ref + drho[r];
+                psi[r] = psi_of(rho[r], P, flag);
+            }
+            s_psi[(ly + 1) * SW + (lx + 1)] = psi[r];
+        }
+        // ---- halo ring: psi only
+#pragma unroll
+        for (int j = 0; j < NHT; ++j) {
+            const int h = tid + j * NT;
+            if (h < NH) {
+                int cx, cy;
+                if (h < SW) {
+                    cx = h;
+                    cy = 0;
+                } else if (h < 2 * SW) {
+                    cx = h - SW;
+                    cy = SH - 1;
+                } else {
+                    const int q = h - 2 * SW;
+                    cy = 1 + (q >> 1);
+                    cx = (q & 1) ? SW - 1 : 0;
+                }
+                float ph = -1.0f;
+                float fh[9];
+                if (tl.x0 - 1 + cx <= g.nx && tl.y0 - 1 + cy <= g.ny && gather(cx - 1, cy - 1, fh))
+                    ph = psi_of(rho_ref + sum9(fh), P, flag);
+                s_psi[cy * SW + cx] = ph;
+            }
+        }
+        __syncthreads();  // stage s consumed, psi tile complete
+
+        if (tid == 0) {
+            const int tn = t + S * gridDim.x;
+            if (tn < A.n_tiles) {
+                fence_proxy_async();  // generic reads of stage s before the async refill
+                issue(tn, s);
+            }
+        }
+        if (flag) atomicOr(&A.status[tl.lat], flag);
+
+        if (x < g.nx) {
+            const float mG = -P.G;
+            const float G2 = P.G * P.G;
+            float* fo = A.fout + g.f_off;
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int ly = threadIdx.y * RY + r;
+                const int y = tl.y0 + ly;
+                if (y >= g.ny || !live[r]) continue;
+                const int c = (ly + 1) * SW + (lx + 1);
+                float gx, gy;
+                force_sum<float>(ms != nullptr, psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
+                                 s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx, gy);
+                const float Fx = mG * psi[r] * gx;
+                const float Fy = mG * psi[r] * gy;
+                collide<float>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
+                store_node<float>(fo, g, x, y, f[r]);
+            }
+        }
+        __syncthreads();  // psi tile is rewritten by the next tile
+    }
+
+    if (failed && tid == 0) {
+        // wait (bounded) for the loads still in flight into this CTA's stages
+        for (int j = 0; j < S; ++j) {
+            const int kk = k + j;
+            const int t = blockIdx.x + kk * gridDim.x;
+            if (t < A.n_tiles) mbar_wait_bounded(&bars[kk % S], (uint32_t)((kk / S) & 1), kWaitLimit);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+template <int TX, int TY, int RY, int S>
+static cudaError_t launch_tma_tile(int grid, const TmaArgs& a, const TmaMaps& maps, cudaStream_t s) {
+    using B = TmaBox<TX, TY>;
+    constexpr int SW = TX + 2, SH = TY + 2;
+    const size_t smem = (size_t)S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
+    static bool configured = false;  // per process; attributes are per device but identical
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<TX, TY, RY, S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    step_tma_kernel<TX, TY, RY, S><<<grid, dim3(TX, TY / RY), smem, s>>>(a, maps);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY, int RY, int S>
+static int tma_occupancy() {
+    using B = TmaBox<TX, TY>;
+    constexpr int SW = TX + 2, SH = TY + 2;
+    const size_t smem = (size_t)S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
+    if (cudaFuncSetAttribute(step_tma_kernel<TX, TY, RY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma_kernel<TX, TY, RY, S>, TX * (TY / RY), smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+// TMA variants: {TX, TY, RY, stages}
+#define LBM_TMA_VARIANTS(X) X(0, 32, 8, 1, 3) X(1, 32, 16, 2, 2) X(2, 64, 8, 1, 2) X(3, 32, 8, 1, 4)
+
+int tma_variant_count() { return 4; }
+
+void tma_variant_shape(int v, int* tx, int* ty) {
+#define LBM_SHAPE(i, a, b, r, s) \
+    if (v == i) {                \
+        *tx = a;                 \
+        *ty = b;                 \
+    }
+    LBM_TMA_VARIANTS(LBM_SHAPE)
+#undef LBM_SHAPE
+}
+
+int tma_blocks_per_sm(int v) {
+#define LBM_OCC(i, a, b, r, s) \
+    if (v == i) return tma_occupancy<a, b, r, s>();
+    LBM_TMA_VARIANTS(LBM_OCC)
+#undef LBM_OCC
+    return 0;
+}
+
+cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps, cudaStream_t s) {
+    if (args.n_tiles <= 0) return cudaSuccess;
+#define LBM_LAUNCH(i, a, b, r, st) \
+    if (v == i) return launch_tma_tile<a, b, r, st>(grid, args, maps, s);
+    LBM_TMA_VARIANTS(LBM_LAUNCH)
+#undef LBM_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+// Tensor maps of one lattice's planes in a distribution buffer (3-D: x, y,
+// population) and of its wall mask (2-D), boxes sized for tile TX x TY.
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn == nullptr) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const float* buf1,
+                         const uint8_t* mask_base, CUtensorMap* fmaps2, CUtensorMap* mmap) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (enc == nullptr) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * kGY), 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 4), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const float* bufs[2] = {buf0, buf1};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = enc(&fmaps2[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)(bufs[b] + g.f_off), dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    if (g.has_mask) {
+        const cuuint64_t mdims[2] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * kGY)};
+        const cuuint64_t mstr[1] = {(cuuint64_t)g.pitch};
+        const cuuint32_t mbox[2] = {(cuuint32_t)(tx + 32), (cuuint32_t)(ty + 4)};
+        const cuuint32_t mestr[2] = {1, 1};
+        CUresult r = enc(mmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)(mask_base + g.mask_off), mdims, mstr, mbox,
+                         mestr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    } else {
+        memset(mmap, 0, sizeof(CUtensorMap));
+    }
+    return true;
+}
+
+}  // namespace lbm

@@ -22,6 +22,7 @@ LBM_ENOMEM = 2
 LBM_ECUDA = 3
 LBM_EPSI_DOMAIN = 4
 LBM_ENONFINITE = 5
+LBM_ETIMEOUT = 6
 
 LBM_FP32_DEV = 0
 LBM_FP32 = 1
@@ -29,6 +30,7 @@ LBM_FP64 = 2
 
 LBM_FLAG_PSI_CLAMPED = 1
 LBM_FLAG_NONFINITE = 2
+LBM_FLAG_TIMEOUT = 4
 
 PRECISIONS = {"fp32_dev": LBM_FP32_DEV, "fp32": LBM_FP32, "fp64": LBM_FP64}
 

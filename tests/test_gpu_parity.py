@@ -77,10 +77,16 @@ def test_fp32_matches_oracle(case, precision):
 
 @pytest.mark.parametrize("precision", ["fp32_dev", "fp64"])
 def test_every_tile_is_bitwise_identical(precision):
-    specs = [small_spec(70, 45, walls=True), small_spec(19, 23)]
+    # includes the TMA-staged persistent FP32 variants, ragged tiles, walls
+    # and a lattice under 4 cells high (ghost frame refreshed separately)
+    specs = [small_spec(70, 45, walls=True), small_spec(19, 23), small_spec(5, 3), small_spec(130, 9)]
     ref = run_gpu(specs, precision, 5, tile=0)
     for t in range(1, lbm.lbm_tile_count()):
-        got = run_gpu(specs, precision, 5, tile=t)
+        try:
+            got = run_gpu(specs, precision, 5, tile=t)
+        except lbm.LbmError as e:  # FP32-only variants on an FP64 context
+            assert precision == "fp64" and e.code == lbm.LBM_EINVAL
+            continue
         for a, b in zip(ref, got):
             for x, y in zip(a, b):
                 assert np.array_equal(x, y), f"tile {lbm.lbm_tile_shape(t)}"
@@ -135,7 +141,7 @@ def test_autotune_keeps_state_and_results():
     b.init()
     b.step(3)
     best, ms = lbm.lbm_autotune(b.ctx, 4)
-    assert 0 <= best < lbm.lbm_tile_count() and all(t > 0 for t in ms)
+    assert 0 <= best < lbm.lbm_tile_count() and all(t > 0 for t in ms), ms
     assert b.info()["steps"] == 3
     b.step(5)
     got = b.moments(0)
