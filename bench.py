@@ -47,7 +47,29 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="time budget of the oracle sample for cpu_baseline")
+    ap.add_argument("--profile", default=None, metavar="WORKLOAD",
+                    help="profiling mode for ncu: only init and --steps FP32 steps of WORKLOAD "
+                         "(coexistence_batch, laplace_batch, collapse_2048x1024, ...) with --tile")
+    ap.add_argument("--tile", type=int, default=None, help="step-kernel tile index for --profile")
     return ap.parse_args()
+
+
+def run_profile(args):
+    """A minimal launch sequence for ncu: one context, init, --steps steps."""
+    import torch
+    from paper_1605_01800_gb300 import inputs, lbm
+    torch.cuda.set_device(0)
+    specs = inputs.WORKLOADS[args.profile]()
+    b = lbm.Batch(specs, "fp32_dev")
+    if args.tile is not None:
+        lbm.lbm_set_tile(b.ctx, args.tile)
+    b.init()
+    b.step(args.steps)
+    lbm.lbm_sync(b.ctx)
+    info = b.info()
+    print(json.dumps({"profile": args.profile, "tile_index": args.tile, "tile": [info["tile_x"], info["tile_y"]],
+                      "steps": args.steps, "nodes": info["nodes"], "launches": info["kernel_launches"]}))
+    b.close()
 
 
 def kernel_source_hash():
@@ -212,6 +234,9 @@ def timed_steps(torch, ctx, lbm, stream, flush, steps):
 
 def main():
     args = parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

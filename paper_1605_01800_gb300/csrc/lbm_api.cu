@@ -93,6 +93,7 @@ struct lbm_ctx {
     double* d_scalar = nullptr;
     double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
     std::vector<Phys<double>> phys_d;
+    PhysTable<float>* h_table = nullptr;  // FP32 parameters as a kernel argument (n <= kParamLattices)
     size_t device_bytes = 0;
 
     cudaStream_t stream = nullptr;
@@ -189,6 +190,7 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->d_phys_f);
     cudaFree(c->d_phys_d);
     cudaFree(c->d_tiles);
+    delete c->h_table;
     for (int v = 0; v < lbm_ctx::kMaxTma; ++v)
         for (int b = 0; b < 2; ++b) delete c->h_maps[v][b];
     cudaFree(c->d_status);
@@ -289,6 +291,11 @@ int upload_phys(lbm_ctx* c) {
     }
     CK(cudaMemcpy(c->d_phys_d, c->phys_d.data(), c->n * sizeof(Phys<double>), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_phys_f, pf.data(), c->n * sizeof(Phys<float>), cudaMemcpyHostToDevice));
+    if (c->n <= kParamLattices) {
+        if (!c->h_table) c->h_table = new PhysTable<float>();
+        memset(c->h_table, 0, sizeof(PhysTable<float>));
+        for (int l = 0; l < c->n; ++l) c->h_table->p[l] = pf[l];
+    }
     return LBM_OK;
 }
 
@@ -309,11 +316,11 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
     } else if (c->tile_index >= kTileCount) {
         const int v = c->tile_index - kTileCount;
         TmaArgs a{c->d_tiles, c->n_tiles, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status};
-        e = launch_step_tma(v, c->tma_grid[v], a, *c->h_maps[v][src], c->stream);
+        e = launch_step_tma(v, c->tma_grid[v], a, *c->h_maps[v][src], *c->h_table, c->stream);
     } else {
         StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
                           (float*)c->f[1 - src], c->d_mask, c->d_status};
-        e = launch_step_f32(c->tile_index, c->n_tiles, a, c->stream);
+        e = launch_step_f32(c->tile_index, c->n_tiles, a, c->h_table, c->stream);
     }
     if (e != cudaSuccess || !c->has_tiny) return e;
     // lattices under 4 cells wide or high: rewrite their ghost frames

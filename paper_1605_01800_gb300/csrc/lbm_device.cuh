@@ -98,12 +98,12 @@ __device__ __forceinline__ float psi_of(float rho, const Phys<float>& P, unsigne
         q = (float)psi_bracket_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b4,
                                     (double)P.cs2);
     float psi2 = P.kpsi * rho * q;
-    if (!(psi2 >= 0.0f && om > 0.0f)) {
-        flag |= (psi2 < 0.0f && om > 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
-        psi2 = 0.0f;
-    } else if (psi2 > 3.0e38f) {
-        flag |= FLAG_NONFINITE;
-    }
+    // flags and clamp as selects (no branches): psi^2 < 0 is clamped; NaN,
+    // overflow or a density past close packing (eta >= 1) is non-finite
+    const bool dense_ok = om > 0.0f;
+    flag |= (psi2 < 0.0f && dense_ok) ? FLAG_PSI_CLAMPED : 0u;
+    flag |= (!(psi2 <= 3.0e38f) || !dense_ok) ? FLAG_NONFINITE : 0u;
+    psi2 = (psi2 > 0.0f && dense_ok) ? psi2 : 0.0f;
     return psi2 > 0.0f ? psi2 * rsqrtf(psi2) : 0.0f;
 }
 
@@ -313,6 +313,167 @@ __device__ __forceinline__ void collide(T f[9], T rho, T drho, T Fx, T Fy, T g2G
     // and the identical rounding of every node of a uniform phase would shift
     // the mass by the same relative amount at every step.
     f[0] = drho - sum8(f);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 arithmetic in explicit IEEE operations, one node (F1) or two nodes per
+// paired instruction (F2: FADD2 / FMUL2 / FFMA2 on sm_100+). Every operation
+// is the same correctly rounded operation in both forms and nothing is left
+// for the compiler to contract, so one node gives bitwise the same result
+// whether it is computed alone or paired with another.
+struct F1 {
+    float v;
+};
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return {__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return {__fsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return {__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ F1 vfma(F1 a, F1 b, F1 c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+// a - b as fma(b, -1, a): the product is exact, so this is round(a - b)
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+
+template <class V> __device__ __forceinline__ V splat(float s);
+template <> __device__ __forceinline__ F1 splat<F1>(float s) { return {s}; }
+template <> __device__ __forceinline__ F2 splat<F2>(float s) { return {make_float2(s, s)}; }
+
+// per-lane helpers: quotient, reciprocal square root, lane access
+__device__ __forceinline__ F1 vdiv(F1 a, F1 b) { return {__fdividef(a.v, b.v)}; }
+__device__ __forceinline__ F2 vdiv(F2 a, F2 b) {
+    return {make_float2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y))};
+}
+__device__ __forceinline__ int lanes(F1) { return 1; }
+__device__ __forceinline__ int lanes(F2) { return 2; }
+__device__ __forceinline__ float lane(F1 a, int) { return a.v; }
+__device__ __forceinline__ float lane(F2 a, int i) { return i == 0 ? a.v.x : a.v.y; }
+__device__ __forceinline__ void set_lane(F1& a, int, float x) { a.v = x; }
+__device__ __forceinline__ void set_lane(F2& a, int i, float x) {
+    if (i == 0) a.v.x = x; else a.v.y = x;
+}
+
+template <class V>
+__device__ __forceinline__ V vsum8(const V f[9]) {
+    return ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+}
+template <class V>
+__device__ __forceinline__ V vsum9(const V f[9]) {
+    return f[0] + vsum8(f);
+}
+
+// psi of Eq. 13 (see psi_of above): the polynomial in explicit operations, the
+// quotient and square root per lane with the fast hardware approximations,
+// the FP64 fallback near the psi = 0 root and the flags per lane.
+template <class V>
+__device__ __forceinline__ V vpsi(V rho, const Phys<float>& P, unsigned& flag) {
+    const V one = splat<V>(1.0f);
+    const V eta = splat<V>(P.b4) * rho;
+    const V om = one - eta;
+    const V num = vfma(eta, vfma(eta, one - eta, one), one);
+    const V C = vdiv(num, (om * om) * om);
+    V q = vfma(splat<V>(P.RT), C, splat<V>(0.0f) - vfma(splat<V>(P.a), rho, splat<V>(P.cs2)));
+    V psi2 = (splat<V>(P.kpsi) * rho) * q;
+    V out;
+#pragma unroll
+    for (int i = 0; i < lanes(V{}); ++i) {
+        float p2 = lane(psi2, i);
+        const float qi = lane(q, i), ri = lane(rho, i);
+        if (fabsf(qi) < 0.0078125f * P.cs2)
+            p2 = __fmul_rn(__fmul_rn(P.kpsi, ri),
+                           (float)psi_bracket_fp64((double)ri, (double)P.RT, (double)P.a, (double)P.b4,
+                                                   (double)P.cs2));
+        const bool dense_ok = lane(om, i) > 0.0f;
+        flag |= (p2 < 0.0f && dense_ok) ? FLAG_PSI_CLAMPED : 0u;
+        flag |= (!(p2 <= 3.0e38f) || !dense_ok) ? FLAG_NONFINITE : 0u;
+        p2 = (p2 > 0.0f && dense_ok) ? p2 : 0.0f;
+        set_lane(out, i, p2 > 0.0f ? __fmul_rn(p2, rsqrtf(p2)) : 0.0f);
+    }
+    return out;
+}
+
+// Force sum of Eq. 7 (see force_sum below) in explicit operations.
+template <class V>
+__device__ __forceinline__ void vforce_sum(V pe, V pn, V pw, V ps, V pne, V pnw, V psw, V pse, V& gx, V& gy) {
+    const V third = splat<V>(1.0f / 3.0f), twelfth = splat<V>(1.0f / 12.0f);
+    gx = vfma(third, pe - pw, twelfth * ((pne - pnw) + (pse - psw)));
+    gy = vfma(third, pn - ps, twelfth * ((pne + pnw) - (psw + pse)));
+}
+
+// The collision of collide<T> (same equations, same order of terms) in
+// explicit operations, for one node (F1) or a pair of nodes (F2).
+template <class V>
+__device__ __forceinline__ void vcollide(V f[9], V rho, V drho, V Fx, V Fy, V g2G2, const Phys<float>& P) {
+    const V half = splat<V>(0.5f), two = splat<V>(2.0f), three = splat<V>(3.0f), four = splat<V>(4.0f);
+    const V sx = f[1] - f[3];
+    const V sy = f[2] - f[4];
+    const V d57 = f[5] - f[7];
+    const V d68 = f[6] - f[8];
+    const V jx = sx + (d57 - d68);
+    const V jy = sy + (d57 + d68);
+    const V rvx = vfma(half, Fx, jx);
+    const V rvy = vfma(half, Fy, jy);
+    const V inv_rho = vdiv(splat<V>(1.0f), rho);
+    const V vx = rvx * inv_rho;
+    const V vy = rvy * inv_rho;
+
+    const V p13 = f[1] + f[3], p24 = f[2] + f[4];
+    const V p57 = f[5] + f[7], p68 = f[6] + f[8];
+    const V a14 = p13 + p24;
+    const V a58 = p57 + p68;
+    const V m1 = vfma(two, a58, splat<V>(0.0f) - vfma(four, f[0], a14));
+    const V m2 = vfma(four, f[0], a58) - two * a14;
+    const V m4 = (d57 - d68) - two * sx;
+    const V m6 = (d57 + d68) - two * sy;
+    const V m7 = p13 - p24;
+    const V m8 = p57 - p68;
+
+    const V ru2 = vfma(rvx, vx, rvy * vy);
+    const V meq1 = vfma(three, ru2, splat<V>(0.0f) - two * drho);
+    const V meq2 = drho - three * ru2;
+    const V meq7 = vfma(rvx, vx, splat<V>(0.0f) - rvy * vy);
+    const V meq8 = rvx * vy;
+
+    const V vF6 = splat<V>(6.0f) * vfma(vx, Fx, vy * Fy);
+    // m* = m - s (m - m_eq) + (1 - s/2) S, then scaled by 1 / |row|^2 of M
+    const V ms1 = vfma(splat<V>(P.li_e), g2G2, vfma(splat<V>(P.h[1]), vF6, m1 - splat<V>(P.s[1]) * (m1 - meq1)));
+    const V ms2 = vfma(splat<V>(-P.li_z), g2G2, m2 - splat<V>(P.s[2]) * (m2 - meq2) - splat<V>(P.h[2]) * vF6);
+    const V ms3 = jx + Fx;
+    const V ms4 = (m4 - splat<V>(P.s[4]) * (m4 + rvx)) - splat<V>(P.h[4]) * Fx;
+    const V ms5 = jy + Fy;
+    const V ms6 = (m6 - splat<V>(P.s[6]) * (m6 + rvy)) - splat<V>(P.h[6]) * Fy;
+    const V S7 = two * vfma(vx, Fx, splat<V>(0.0f) - vy * Fy);
+    const V S8 = vfma(vx, Fy, vy * Fx);
+    const V ms7 = vfma(splat<V>(P.h[7]), S7, m7 - splat<V>(P.s[7]) * (m7 - meq7));
+    const V ms8 = vfma(splat<V>(P.h[8]), S8, m8 - splat<V>(P.s[8]) * (m8 - meq8));
+
+    const V a0 = drho * splat<V>(1.0f / 9.0f);
+    const V a1 = ms1 * splat<V>(1.0f / 36.0f);
+    const V a2 = ms2 * splat<V>(1.0f / 36.0f);
+    const V a3 = ms3 * splat<V>(1.0f / 6.0f);
+    const V a4 = ms4 * splat<V>(1.0f / 12.0f);
+    const V a5 = ms5 * splat<V>(1.0f / 6.0f);
+    const V a6 = ms6 * splat<V>(1.0f / 12.0f);
+    const V a7 = ms7 * splat<V>(0.25f);
+    const V a8 = ms8 * splat<V>(0.25f);
+    const V axis = (a0 - a1) - two * a2;
+    const V diag = vfma(two, a1, a0) + a2;
+    const V px = a3 - two * a4;
+    const V py = a5 - two * a6;
+    const V qx = a3 + a4;
+    const V qy = a5 + a6;
+    f[1] = (axis + px) + a7;
+    f[2] = (axis + py) - a7;
+    f[3] = (axis - px) + a7;
+    f[4] = (axis - py) - a7;
+    f[5] = ((diag + qx) + qy) + a8;
+    f[6] = ((diag - qx) + qy) - a8;
+    f[7] = ((diag - qx) - qy) + a8;
+    f[8] = ((diag + qx) - qy) - a8;
+    // f*_0 as the remainder of the conserved density (see collide)
+    f[0] = drho - vsum8(f);
 }
 
 // Force sum g = sum_a w_a psi(x + e_a) e_a of Eq. 7 from the nine psi values

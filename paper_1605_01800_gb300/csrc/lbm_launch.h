@@ -20,6 +20,8 @@ constexpr int kTiles[kTileCount][3] = {
 
 template <typename T>
 struct StepArgs;
+template <typename T>
+struct PhysTable;
 
 // TMA-staged persistent FP32 variants (lbm_step_tma.cu); tile indices
 // kTileCount .. kTileCount + tma_variant_count() - 1 of the public tile list.
@@ -41,13 +43,17 @@ struct TmaMaps {
 int tma_variant_count();
 void tma_variant_shape(int v, int* tx, int* ty);
 int tma_blocks_per_sm(int v);
-cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps, cudaStream_t s);
+cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps,
+                            const PhysTable<float>& table, cudaStream_t s);
 // Tensor maps of lattice g in both buffers (fmaps2[0..1]) and of its mask
 // (mmap; zeroed when the lattice has no mask), boxes for a tx x ty tile.
 bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const float* buf1,
                          const uint8_t* mask_base, CUtensorMap* fmaps2, CUtensorMap* mmap);
 
-cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a, cudaStream_t s);
+// table: the batch's parameters for the constant-bank path (batches of at
+// most kParamLattices lattices), or null to read them from global memory.
+cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a,
+                            const PhysTable<float>* table, cudaStream_t s);
 cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s);
 
 // Lattices [lat0, lat0 + n_lat) of a context, for the FP64 helper kernels.

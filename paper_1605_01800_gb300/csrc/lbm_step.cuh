@@ -14,9 +14,26 @@
 // any of them is used.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// Per-lattice parameters as a kernel parameter (constant bank): indexed by
+// the CTA's lattice, a warp-uniform value, they load once into uniform
+// registers instead of being re-read from global memory under register
+// pressure. Used when a batch has at most kParamLattices lattices.
+constexpr int kParamLattices = 64;
+template <typename T>
+struct PhysTable {
+    Phys<T> p[kParamLattices];
+};
+struct NoTable {
+    int unused;
+};
+template <typename T, bool TABLE>
+using TableOf = typename std::conditional<TABLE, PhysTable<T>, NoTable>::type;
 
 template <typename T>
 struct StepArgs {
@@ -31,9 +48,148 @@ struct StepArgs {
 
 // Register cap for the FP32 kernel with up to two nodes per thread: 64 per
 // thread, so that 1024 threads per SM are resident.
-template <typename T, int TX, int TYT, int RY>
+// ---- FP32 node math shared by the plain-load and the TMA kernels: nodes are
+// processed in pairs (paired FP32 instructions) when a thread owns an even
+// number of them, one at a time otherwise, with bitwise equal results.
+
+// drho, rho, psi of a thread's RY own nodes; a node that is not live reads as
+// density rho_ref and gets the solid/absent sentinel psi = -1.
+template <int RY>
+__device__ __forceinline__ void f32_rho_psi(const float (&f)[RY][9], const bool (&live)[RY], float rho_ref,
+                                            const Phys<float>& P, unsigned& flag, float (&drho)[RY],
+                                            float (&rho)[RY], float (&psi)[RY]) {
+    if constexpr (RY % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < RY; r += 2) {
+            F2 v[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+                v[a].v = make_float2(live[r] ? f[r][a] : 0.0f, live[r + 1] ? f[r + 1][a] : 0.0f);
+            const F2 d = vsum9(v);
+            const F2 rh = splat<F2>(rho_ref) + d;
+            const F2 ps = vpsi(rh, P, flag);
+            drho[r] = d.v.x;
+            drho[r + 1] = d.v.y;
+            rho[r] = rh.v.x;
+            rho[r + 1] = rh.v.y;
+            psi[r] = live[r] ? ps.v.x : -1.0f;
+            psi[r + 1] = live[r + 1] ? ps.v.y : -1.0f;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            F1 v[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v[a].v = live[r] ? f[r][a] : 0.0f;
+            const F1 d = vsum9(v);
+            const F1 rh = splat<F1>(rho_ref) + d;
+            const F1 ps = vpsi(rh, P, flag);
+            drho[r] = d.v;
+            rho[r] = rh.v;
+            psi[r] = live[r] ? ps.v : -1.0f;
+        }
+    }
+}
+
+// psi of one halo cell from its pulled populations
+__device__ __forceinline__ float f32_halo_psi(const float (&fh)[9], float rho_ref, const Phys<float>& P,
+                                              unsigned& flag) {
+    F1 v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a].v = fh[a];
+    return vpsi(splat<F1>(rho_ref) + vsum9(v), P, flag).v;
+}
+
+// psi of the 8 neighbours of the node at s_psi index c (row stride SW), with
+// a solid neighbour (sentinel < 0) replaced by the node's own psi
+template <int SW>
+__device__ __forceinline__ void f32_neighbours(const float* s_psi, int c, float own, bool walls, float (&nb)[8]) {
+    nb[0] = s_psi[c + 1];
+    nb[1] = s_psi[c + SW];
+    nb[2] = s_psi[c - 1];
+    nb[3] = s_psi[c - SW];
+    nb[4] = s_psi[c + SW + 1];
+    nb[5] = s_psi[c + SW - 1];
+    nb[6] = s_psi[c - SW - 1];
+    nb[7] = s_psi[c - SW + 1];
+    if (walls) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) nb[k] = nb[k] < 0.0f ? own : nb[k];
+    }
+}
+
+// Force (Eq. 7), collision (Eq. 3) and store of the thread's RY own nodes.
+// (lx, ly0): tile-local position of the first node; s_psi the psi tile with
+// a one-cell frame (row stride SW); x, y0: lattice position.
+template <int RY, int SW>
+__device__ __forceinline__ void f32_collide_store(float (&f)[RY][9], const bool (&live)[RY],
+                                                  const float (&drho)[RY], const float (&rho)[RY],
+                                                  const float (&psi)[RY], const float* s_psi, int lx, int ly0,
+                                                  bool walls, const Phys<float>& P, float* fo, const Geom& g,
+                                                  int x, int y0) {
+    const float mG = -P.G;
+    const float G2 = __fmul_rn(P.G, P.G);
+    if constexpr (RY % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < RY; r += 2) {
+            const bool do0 = live[r] && y0 + r < g.ny;
+            const bool do1 = live[r + 1] && y0 + r + 1 < g.ny;
+            if (!(do0 || do1)) continue;
+            const int c0 = (ly0 + r + 1) * SW + (lx + 1);
+            float n0[8], n1[8];
+            f32_neighbours<SW>(s_psi, c0, psi[r], walls, n0);
+            f32_neighbours<SW>(s_psi, c0 + SW, psi[r + 1], walls, n1);
+            F2 nb[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) nb[k].v = make_float2(n0[k], n1[k]);
+            F2 gx, gy;
+            vforce_sum(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], nb[6], nb[7], gx, gy);
+            const F2 ps = {make_float2(psi[r], psi[r + 1])};
+            const F2 mGpsi = splat<F2>(mG) * ps;
+            const F2 Fx = mGpsi * gx, Fy = mGpsi * gy;
+            const F2 g2G2 = splat<F2>(G2) * vfma(gx, gx, gy * gy);
+            F2 v[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v[a].v = make_float2(f[r][a], f[r + 1][a]);
+            vcollide(v, F2{make_float2(rho[r], rho[r + 1])}, F2{make_float2(drho[r], drho[r + 1])}, Fx, Fy,
+                     g2G2, P);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                f[r][a] = v[a].v.x;
+                f[r + 1][a] = v[a].v.y;
+            }
+            if (do0) store_node<float>(fo, g, x, y0 + r, f[r]);
+            if (do1) store_node<float>(fo, g, x, y0 + r + 1, f[r + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            if (!(live[r] && y0 + r < g.ny)) continue;
+            const int c = (ly0 + r + 1) * SW + (lx + 1);
+            float n[8];
+            f32_neighbours<SW>(s_psi, c, psi[r], walls, n);
+            F1 nb[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) nb[k].v = n[k];
+            F1 gx, gy;
+            vforce_sum(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], nb[6], nb[7], gx, gy);
+            const F1 mGpsi = splat<F1>(mG) * F1{psi[r]};
+            const F1 Fx = mGpsi * gx, Fy = mGpsi * gy;
+            const F1 g2G2 = splat<F1>(G2) * vfma(gx, gx, gy * gy);
+            F1 v[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) v[a].v = f[r][a];
+            vcollide(v, F1{rho[r]}, F1{drho[r]}, Fx, Fy, g2G2, P);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) f[r][a] = v[a].v;
+            store_node<float>(fo, g, x, y0 + r, f[r]);
+        }
+    }
+}
+
+template <typename T, int TX, int TYT, int RY, bool TABLE>
 __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 && RY <= 2) ? 1024 / (TX * TYT) : 1)
-    step_kernel(StepArgs<T> A) {
+    step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT) {
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
@@ -45,7 +201,11 @@ __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 && RY <= 2) ? 1024 /
     const Geom g = A.geom[tile.lat];
     // restrict: the stores to fout cannot alias the parameters, so they need
     // not be reloaded after every store
-    const Phys<T>* __restrict__ Pp = A.phys + tile.lat;
+    const Phys<T>* __restrict__ Pp;
+    if constexpr (TABLE)
+        Pp = &PT.p[tile.lat];
+    else
+        Pp = A.phys + tile.lat;
     const Phys<T>& P = *Pp;
     const T* __restrict__ fin = A.fin + g.f_off;
     const uint8_t* __restrict__ mask = g.has_mask ? A.mask + g.mask_off : nullptr;
@@ -96,26 +256,33 @@ __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 && RY <= 2) ? 1024 /
             T fh[9];
             if (hx <= nx && hy <= ny &&
                 !pull_node<T>(fin, mask, plane, pitch, node_index(g, hx, hy), fh)) {
-                const T rh = rho_ref + sum9(fh);
-                ph[k] = psi_of(rh, P, flag);
+                if constexpr (std::is_same<T, float>::value)
+                    ph[k] = f32_halo_psi(fh, rho_ref, P, flag);
+                else
+                    ph[k] = psi_of(rho_ref + sum9(fh), P, flag);
             }
         }
     }
 
     // ---- own nodes: density and psi
     T drho[RY], rho[RY], psi[RY];
+    if constexpr (std::is_same<T, float>::value) {
+        f32_rho_psi<RY>(f, live, rho_ref, P, flag, drho, rho, psi);
+    } else {
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        drho[r] = T(0);
-        rho[r] = T(0);
-        psi[r] = T(-1);
-        if (live[r]) {
-            drho[r] = sum9(f[r]);
-            rho[r] = rho_ref + drho[r];
-            psi[r] = psi_of(rho[r], P, flag);
+        for (int r = 0; r < RY; ++r) {
+            drho[r] = T(0);
+            rho[r] = T(0);
+            psi[r] = T(-1);
+            if (live[r]) {
+                drho[r] = sum9(f[r]);
+                rho[r] = rho_ref + drho[r];
+                psi[r] = psi_of(rho[r], P, flag);
+            }
         }
-        s_psi[(threadIdx.y * RY + r + 1) * SW + (lx + 1)] = psi[r];
     }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) s_psi[(threadIdx.y * RY + r + 1) * SW + (lx + 1)] = psi[r];
 #pragma unroll
     for (int k = 0; k < (NH + NT - 1) / NT; ++k)
         if (hc[k] >= 0) s_psi[hc[k]] = ph[k];
@@ -124,25 +291,29 @@ __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 && RY <= 2) ? 1024 /
     if (flag) atomicOr(&A.status[tile.lat], flag);
     if (x >= nx) return;
 
-    const T mG = -P.G;
-    const T G2 = P.G * P.G;
     T* __restrict__ fo = A.fout + g.f_off;
+    if constexpr (std::is_same<T, float>::value) {
+        f32_collide_store<RY, SW>(f, live, drho, rho, psi, s_psi, lx, threadIdx.y * RY, mask != nullptr, P, fo, g,
+                                  x, y0);
+    } else {
+        const T mG = -P.G;
+        const T G2 = P.G * P.G;
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        const int y = y0 + r;
-        if (y >= ny || !live[r]) continue;
-        // ---- force, Eq. 7
-        const int c = (threadIdx.y * RY + r + 1) * SW + (lx + 1);
-        T gx, gy;
-        force_sum<T>(mask != nullptr, psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
-                     s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx,
-                     gy);
-        const T Fx = mG * psi[r] * gx;
-        const T Fy = mG * psi[r] * gy;
-        // ---- collision, Eq. 3
-        collide<T>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
-        // ---- store f* (and its ghost images near an edge)
-        store_node<T>(fo, g, x, y, f[r]);
+        for (int r = 0; r < RY; ++r) {
+            const int y = y0 + r;
+            if (y >= ny || !live[r]) continue;
+            // ---- force, Eq. 7
+            const int c = (threadIdx.y * RY + r + 1) * SW + (lx + 1);
+            T gx, gy;
+            force_sum<T>(mask != nullptr, psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
+                         s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx, gy);
+            const T Fx = mG * psi[r] * gx;
+            const T Fy = mG * psi[r] * gy;
+            // ---- collision, Eq. 3
+            collide<T>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
+            // ---- store f* (and its ghost images near an edge)
+            store_node<T>(fo, g, x, y, f[r]);
+        }
     }
 }
 

@@ -4,24 +4,37 @@
 
 namespace lbm {
 
-template <int TX, int TYT, int RY>
-static cudaError_t launch_tile(int n_tiles, const StepArgs<float>& a, cudaStream_t s) {
-    step_kernel<float, TX, TYT, RY><<<n_tiles, dim3(TX, TYT), 0, s>>>(a);
+template <int TX, int TYT, int RY, bool TABLE>
+static cudaError_t launch_tile(int n_tiles, const StepArgs<float>& a, const PhysTable<float>* table,
+                               cudaStream_t s) {
+    TableOf<float, TABLE> t{};
+    if constexpr (TABLE) t = *table;
+    step_kernel<float, TX, TYT, RY, TABLE><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a, cudaStream_t s) {
+cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& args,
+                            const PhysTable<float>* table, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     switch (tile_index) {
-    case 0: return launch_tile<32, 8, 2>(n_tiles, a, s);
-    case 1: return launch_tile<32, 8, 1>(n_tiles, a, s);
-    case 2: return launch_tile<64, 4, 2>(n_tiles, a, s);
-    case 3: return launch_tile<64, 4, 1>(n_tiles, a, s);
-    case 4: return launch_tile<32, 16, 1>(n_tiles, a, s);
-    case 5: return launch_tile<32, 4, 2>(n_tiles, a, s);
-    case 6: return launch_tile<32, 8, 4>(n_tiles, a, s);
-    case 7: return launch_tile<64, 8, 1>(n_tiles, a, s);
-    case 8: return launch_tile<128, 2, 2>(n_tiles, a, s);
+    case 0: return table ? launch_tile<32, 8, 2, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 8, 2, false>(n_tiles, args, nullptr, s);
+    case 1: return table ? launch_tile<32, 8, 1, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 8, 1, false>(n_tiles, args, nullptr, s);
+    case 2: return table ? launch_tile<64, 4, 2, true>(n_tiles, args, table, s)
+                   : launch_tile<64, 4, 2, false>(n_tiles, args, nullptr, s);
+    case 3: return table ? launch_tile<64, 4, 1, true>(n_tiles, args, table, s)
+                   : launch_tile<64, 4, 1, false>(n_tiles, args, nullptr, s);
+    case 4: return table ? launch_tile<32, 16, 1, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 16, 1, false>(n_tiles, args, nullptr, s);
+    case 5: return table ? launch_tile<32, 4, 2, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 4, 2, false>(n_tiles, args, nullptr, s);
+    case 6: return table ? launch_tile<32, 8, 4, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 8, 4, false>(n_tiles, args, nullptr, s);
+    case 7: return table ? launch_tile<64, 8, 1, true>(n_tiles, args, table, s)
+                   : launch_tile<64, 8, 1, false>(n_tiles, args, nullptr, s);
+    case 8: return table ? launch_tile<128, 2, 2, true>(n_tiles, args, table, s)
+                   : launch_tile<128, 2, 2, false>(n_tiles, args, nullptr, s);
     default: return cudaErrorInvalidValue;
     }
 }

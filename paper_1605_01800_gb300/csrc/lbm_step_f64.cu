@@ -6,22 +6,22 @@ namespace lbm {
 
 template <int TX, int TYT, int RY>
 static cudaError_t launch_tile(int n_tiles, const StepArgs<double>& a, cudaStream_t s) {
-    step_kernel<double, TX, TYT, RY><<<n_tiles, dim3(TX, TYT), 0, s>>>(a);
+    step_kernel<double, TX, TYT, RY, false><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, NoTable{0});
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s) {
+cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& args, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     switch (tile_index) {
-    case 0: return launch_tile<32, 8, 2>(n_tiles, a, s);
-    case 1: return launch_tile<32, 8, 1>(n_tiles, a, s);
-    case 2: return launch_tile<64, 4, 2>(n_tiles, a, s);
-    case 3: return launch_tile<64, 4, 1>(n_tiles, a, s);
-    case 4: return launch_tile<32, 16, 1>(n_tiles, a, s);
-    case 5: return launch_tile<32, 4, 2>(n_tiles, a, s);
-    case 6: return launch_tile<32, 8, 4>(n_tiles, a, s);
-    case 7: return launch_tile<64, 8, 1>(n_tiles, a, s);
-    case 8: return launch_tile<128, 2, 2>(n_tiles, a, s);
+    case 0: return launch_tile<32, 8, 2>(n_tiles, args, s);
+    case 1: return launch_tile<32, 8, 1>(n_tiles, args, s);
+    case 2: return launch_tile<64, 4, 2>(n_tiles, args, s);
+    case 3: return launch_tile<64, 4, 1>(n_tiles, args, s);
+    case 4: return launch_tile<32, 16, 1>(n_tiles, args, s);
+    case 5: return launch_tile<32, 4, 2>(n_tiles, args, s);
+    case 6: return launch_tile<32, 8, 4>(n_tiles, args, s);
+    case 7: return launch_tile<64, 8, 1>(n_tiles, args, s);
+    case 8: return launch_tile<128, 2, 2>(n_tiles, args, s);
     default: return cudaErrorInvalidValue;
     }
 }

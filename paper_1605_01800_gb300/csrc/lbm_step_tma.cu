@@ -117,7 +117,7 @@ struct TmaBox {
 
 template <int TX, int TY, int RY, int S>
 __global__ void __launch_bounds__(TX*(TY / RY), 1)
-    step_tma_kernel(const TmaArgs A, const __grid_constant__ TmaMaps M) {
+    step_tma_kernel(const TmaArgs A, const __grid_constant__ TmaMaps M, const __grid_constant__ PhysTable<float> PT) {
     using B = TmaBox<TX, TY>;
     constexpr int TYT = TY / RY;
     constexpr int NT = TX * TYT;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
         }
         const Tile tl = A.tiles[t];
         const Geom g = A.geom[tl.lat];
-        const Phys<float>* __restrict__ Pp = A.phys + tl.lat;
+        const Phys<float>* __restrict__ Pp = &PT.p[tl.lat];
         const Phys<float>& P = *Pp;
         const float* __restrict__ st = reinterpret_cast<const float*>(smem + s * B::STAGE_BYTES);
         const uint8_t* __restrict__ ms =
@@ -208,16 +208,10 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
             const int y = tl.y0 + ly;
             live[r] = (x <= g.nx) && (y <= g.ny);
             if (live[r]) live[r] = gather(lx, ly, f[r]);
-            drho[r] = 0.0f;
-            rho[r] = 0.0f;
-            psi[r] = -1.0f;
-            if (live[r]) {
-                drho[r] = sum9(f[r]);
-                rho[r] = rho_ref + drho[r];
-                psi[r] = psi_of(rho[r], P, flag);
-            }
-            s_psi[(ly + 1) * SW + (lx + 1)] = psi[r];
         }
+        f32_rho_psi<RY>(f, live, rho_ref, P, flag, drho, rho, psi);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) s_psi[(threadIdx.y * RY + r + 1) * SW + (lx + 1)] = psi[r];
         // ---- halo ring: psi only
 #pragma unroll
         for (int j = 0; j < NHT; ++j) {
@@ -238,7 +232,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
                 float ph = -1.0f;
                 float fh[9];
                 if (tl.x0 - 1 + cx <= g.nx && tl.y0 - 1 + cy <= g.ny && gather(cx - 1, cy - 1, fh))
-                    ph = psi_of(rho_ref + sum9(fh), P, flag);
+                    ph = f32_halo_psi(fh, rho_ref, P, flag);
                 s_psi[cy * SW + cx] = ph;
             }
         }
@@ -253,25 +247,9 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
         }
         if (flag) atomicOr(&A.status[tl.lat], flag);
 
-        if (x < g.nx) {
-            const float mG = -P.G;
-            const float G2 = P.G * P.G;
-            float* fo = A.fout + g.f_off;
-#pragma unroll
-            for (int r = 0; r < RY; ++r) {
-                const int ly = threadIdx.y * RY + r;
-                const int y = tl.y0 + ly;
-                if (y >= g.ny || !live[r]) continue;
-                const int c = (ly + 1) * SW + (lx + 1);
-                float gx, gy;
-                force_sum<float>(ms != nullptr, psi[r], s_psi[c + 1], s_psi[c + SW], s_psi[c - 1], s_psi[c - SW],
-                                 s_psi[c + SW + 1], s_psi[c + SW - 1], s_psi[c - SW - 1], s_psi[c - SW + 1], gx, gy);
-                const float Fx = mG * psi[r] * gx;
-                const float Fy = mG * psi[r] * gy;
-                collide<float>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
-                store_node<float>(fo, g, x, y, f[r]);
-            }
-        }
+        if (x < g.nx)
+            f32_collide_store<RY, SW>(f, live, drho, rho, psi, s_psi, lx, threadIdx.y * RY, ms != nullptr, P,
+                                      A.fout + g.f_off, g, x, tl.y0 + threadIdx.y * RY);
         __syncthreads();  // psi tile is rewritten by the next tile
     }
 
@@ -288,7 +266,8 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
 // ---------------------------------------------------------------- host side
 
 template <int TX, int TY, int RY, int S>
-static cudaError_t launch_tma_tile(int grid, const TmaArgs& a, const TmaMaps& maps, cudaStream_t s) {
+static cudaError_t launch_tma_tile(int grid, const TmaArgs& a, const TmaMaps& maps, const PhysTable<float>& table,
+                                   cudaStream_t s) {
     using B = TmaBox<TX, TY>;
     constexpr int SW = TX + 2, SH = TY + 2;
     const size_t smem = (size_t)S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
@@ -299,7 +278,7 @@ static cudaError_t launch_tma_tile(int grid, const TmaArgs& a, const TmaMaps& ma
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    step_tma_kernel<TX, TY, RY, S><<<grid, dim3(TX, TY / RY), smem, s>>>(a, maps);
+    step_tma_kernel<TX, TY, RY, S><<<grid, dim3(TX, TY / RY), smem, s>>>(a, maps, table);
     return cudaGetLastError();
 }
 
@@ -345,10 +324,11 @@ int tma_blocks_per_sm(int v) {
     return 0;
 }
 
-cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps, cudaStream_t s) {
+cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps,
+                            const PhysTable<float>& table, cudaStream_t s) {
     if (args.n_tiles <= 0) return cudaSuccess;
 #define LBM_LAUNCH(i, a, b, r, st) \
-    if (v == i) return launch_tma_tile<a, b, r, st>(grid, args, maps, s);
+    if (v == i) return launch_tma_tile<a, b, r, st>(grid, args, maps, table, s);
     LBM_TMA_VARIANTS(LBM_LAUNCH)
 #undef LBM_LAUNCH
     return cudaErrorInvalidValue;
