@@ -79,14 +79,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
+def profiled_traffic(tile):
+    """DRAM bytes per launch of the step kernel with tile index `tile` from the
+    committed ncu summary, or None when the kernel source changed since that
+    capture or that tile was not captured."""
     if not os.path.exists(PROFILE):
         return None
     text = open(PROFILE).read()
     m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch\[%d\]:\s*([0-9.eE+]+)" % tile, text)
     if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_bytes.group(1))
@@ -376,7 +377,7 @@ def main():
     for v in large.values():
         v["frac"] = v["achieved_gbs"] / peak
     achieved = ALG_BYTES_FP32 * nodes / (ms_per_step * 1e-3) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(best_tile)
 
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
