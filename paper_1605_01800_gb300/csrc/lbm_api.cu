@@ -92,6 +92,8 @@ struct lbm_ctx {
     double* d_partials = nullptr;
     double* d_scalar = nullptr;
     double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
+    double* d_psi = nullptr;     // read-out scratch: one ghosted FP64 plane per lattice
+    unsigned* d_bad = nullptr;   // per-lattice invalid-input flags of the init kernel
     std::vector<Phys<double>> phys_d;
     PhysTable<float>* h_table = nullptr;  // FP32 parameters as a kernel argument (n <= kParamLattices)
     size_t device_bytes = 0;
@@ -197,6 +199,8 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_scalar);
     cudaFree(c->d_io);
+    cudaFree(c->d_psi);
+    cudaFree(c->d_bad);
     delete c;
 }
 
@@ -301,10 +305,13 @@ int upload_phys(lbm_ctx* c) {
 
 // One step launch from buffer `src` into buffer 1 - src.
 LaunchSet launch_set(lbm_ctx* c, int lat0, int n_lat) {
-    long long mx = 0;
-    for (int l = lat0; l < lat0 + n_lat; ++l)
-        mx = std::max(mx, (long long)c->lats[l].geom.nx * c->lats[l].geom.ny);
-    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx};
+    long long mx = 0, me = 0;
+    for (int l = lat0; l < lat0 + n_lat; ++l) {
+        const Geom& g = c->lats[l].geom;
+        mx = std::max(mx, (long long)g.nx * g.ny);
+        me = std::max(me, (long long)g.nx + g.ny);
+    }
+    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx, me};
 }
 
 cudaError_t launch_one_step(lbm_ctx* c, int src) {
@@ -375,11 +382,12 @@ int read_status(lbm_ctx* c, std::vector<unsigned>& out) {
     return LBM_OK;
 }
 
-// Validate lattice `lat`'s host fields (fluid nodes only) and resolve an
-// automatic FP32 deviation reference (minimum density).
-int check_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy,
-                 bool* phys_changed) {
+// Resolve an automatic FP32 deviation reference (the minimum density over
+// fluid nodes) from lattice `lat`'s host field; the inputs themselves are
+// validated on the device by the init kernel.
+int resolve_rho_ref(lbm_ctx* c, int lat, const double* rho, bool* phys_changed) {
     HostLattice& L = c->lats[lat];
+    if (!(c->precision == LBM_FP32_DEV && L.rho_ref_auto)) return LBM_OK;
     const long long n = (long long)L.geom.nx * L.geom.ny;
     const uint8_t* m = L.mask.empty() ? nullptr : L.mask.data();
     double rmin = HUGE_VAL;
@@ -387,17 +395,14 @@ int check_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const
         if (m && m[i]) continue;
         if (!(std::isfinite(rho[i]) && rho[i] > 0.0))
             return fail(LBM_EINVAL, "lattice %d: rho[%lld]=%g must be finite and > 0", lat, i, rho[i]);
-        if ((ux && !std::isfinite(ux[i])) || (uy && !std::isfinite(uy[i])))
-            return fail(LBM_EINVAL, "lattice %d: velocity at %lld is not finite", lat, i);
         rmin = std::min(rmin, rho[i]);
     }
-    if (c->precision == LBM_FP32_DEV && L.rho_ref_auto) {
-        L.rho_ref = std::isfinite(rmin) ? (double)(float)rmin : 0.0;
-        L.rho_ref_auto = false;
-        *phys_changed = true;
-    }
+    L.rho_ref = std::isfinite(rmin) ? (double)(float)rmin : 0.0;
+    L.rho_ref_auto = false;
+    *phys_changed = true;
     return LBM_OK;
 }
+
 
 long long range_nodes(lbm_ctx* c, int lat0, int n_lat) {
     const Geom& last = c->lats[lat0 + n_lat - 1].geom;
@@ -410,7 +415,7 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
     bool changed = false;
     for (int l = lat0; l < lat0 + n_lat; ++l) {
         const long long o = c->lats[l].geom.node_off - c->lats[lat0].geom.node_off;
-        int rc = check_fields(c, l, rho + o, ux ? ux + o : nullptr, uy ? uy + o : nullptr, &changed);
+        int rc = resolve_rho_ref(c, l, rho + o, &changed);
         if (rc) return rc;
     }
     if (changed) {
@@ -427,13 +432,16 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
     if (ux) CK(cudaMemcpyAsync(d_ux, ux, bytes, cudaMemcpyHostToDevice, c->stream));
     if (uy) CK(cudaMemcpyAsync(d_uy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
     const LaunchSet ls = launch_set(c, lat0, n_lat);
+    CK(cudaMemsetAsync(c->d_bad, 0, c->n * sizeof(unsigned), c->stream));
     cudaError_t e;
     if (c->precision == LBM_FP64)
         e = launch_init_f64(ls, c->d_io, ux ? c->d_io + c->total_nodes : nullptr,
-                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (double*)c->f[c->cur], c->stream);
+                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (double*)c->f[c->cur], c->d_bad,
+                            c->stream);
     else
         e = launch_init_f32(ls, c->d_io, ux ? c->d_io + c->total_nodes : nullptr,
-                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (float*)c->f[c->cur], c->stream);
+                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (float*)c->f[c->cur], c->d_bad,
+                            c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     c->launches += 1;
     if (c->has_tiny) {  // lattices under 4 cells: their ghost frames are written separately
@@ -442,8 +450,16 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
         if (e != cudaSuccess) return cuda_fail(e, "ghost refresh kernel");
         c->launches += 1;
     }
-    // the host arrays may be pageable and the staging buffer is reused: wait
+    // the host arrays may be pageable and the staging buffer is reused: wait,
+    // then report invalid input found by the init kernel
+    std::vector<unsigned> bad(c->n, 0u);
+    CK(cudaMemcpyAsync(bad.data(), c->d_bad, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    for (int l = lat0; l < lat0 + n_lat; ++l)
+        if (bad[l])
+            return fail(LBM_EINVAL,
+                        "lattice %d: a fluid density is not finite and > 0, or a velocity is not finite "
+                        "(the lattice's state is undefined until the next successful init)", l);
     return LBM_OK;
 }
 
@@ -451,16 +467,15 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
 // lattice lat0's first node: one kernel launch, one download per field.
 int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, double* uy, double* p) {
     const long long N = c->total_nodes;
-    double* d[4] = {rho ? c->d_io : nullptr, ux ? c->d_io + N : nullptr, uy ? c->d_io + 2 * N : nullptr,
-                    p ? c->d_io + 3 * N : nullptr};
+    double* d[4] = {c->d_io, c->d_io + N, c->d_io + 2 * N, c->d_io + 3 * N};
     const LaunchSet ls = launch_set(c, lat0, n_lat);
     cudaError_t e;
     if (c->precision == LBM_FP64)
-        e = launch_moments_f64(ls, (const double*)c->f[c->cur], d[0], d[1], d[2], d[3], c->stream);
+        e = launch_moments_f64(ls, (const double*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream);
     else
-        e = launch_moments_f32(ls, (const float*)c->f[c->cur], d[0], d[1], d[2], d[3], c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "moments kernel");
-    c->launches += 1;
+        e = launch_moments_f32(ls, (const float*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
+    c->launches += 2;
     const long long base = c->lats[lat0].geom.node_off;
     const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
     double* h[4] = {rho, ux, uy, p};
@@ -552,6 +567,8 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (!rc) rc = dev_alloc(c, &c->d_partials, kMassBlocks * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_scalar, sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->total_nodes * sizeof(double));
+    if (!rc) rc = dev_alloc(c, &c->d_psi, ((size_t)c->total_elems / 9 + 64) * sizeof(double));
+    if (!rc) rc = dev_alloc(c, &c->d_bad, n * sizeof(unsigned));
     if (rc) {
         free_ctx(c);
         return rc;

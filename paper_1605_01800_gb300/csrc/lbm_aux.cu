@@ -27,11 +27,14 @@ __device__ __forceinline__ double feq(int a, double rho, double ux, double uy) {
 // x - e_a is solid. To make that pull return f_eq at every fluid node, the
 // stored value at node y for population b is f_eq_b of the node y + e_b it
 // streams into, or f_eq_bbar(y) when y + e_b is solid (the reflected link).
+// With u = 0 (ux, uy null) f_eq_b = w_b rho, and the stored deviation is
+// w_b (rho - rho_ref). Invalid input (a fluid density that is not finite and
+// > 0, a non-finite velocity) sets bad[lat].
 template <typename T>
 __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                             int lat0, const double* __restrict__ rho, const double* __restrict__ ux,
                             const double* __restrict__ uy, const uint8_t* __restrict__ mask_base,
-                            T* __restrict__ f_base) {
+                            T* __restrict__ f_base, unsigned* __restrict__ bad) {
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const double rho_ref = phys[lat].rho_ref;
@@ -41,6 +44,7 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
     if (ux) ux += g.node_off;
     if (uy) uy += g.node_off;
     const long long n = (long long)g.nx * g.ny;
+    unsigned invalid = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % g.nx), y = (int)(i / g.nx);
@@ -50,19 +54,23 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
             store_node<T>(f, g, x, y, out);
             continue;
         }
+        if (!(isfinite(rho[i]) && rho[i] > 0.0)) invalid = 1;
+        if ((ux && !isfinite(ux[i])) || (uy && !isfinite(uy[i]))) invalid = 1;
         for (int b = 0; b < 9; ++b) {
             const int xt = wrap_index(x + kEx[b], g.nx), yt = wrap_index(y + kEy[b], g.ny);
+            const bool back = is_solid(mask, g, xt, yt);
+            const long long j = back ? i : (long long)yt * g.nx + xt;
+            const int bb = back ? kOpp[b] : b;
             double v;
-            if (is_solid(mask, g, xt, yt)) {
-                v = feq(kOpp[b], rho[i], ux ? ux[i] : 0.0, uy ? uy[i] : 0.0);
-            } else {
-                const long long j = (long long)yt * g.nx + xt;
-                v = feq(b, rho[j], ux ? ux[j] : 0.0, uy ? uy[j] : 0.0);
-            }
-            out[b] = (T)(v - kWeq[b] * rho_ref);
+            if (ux == nullptr && uy == nullptr)
+                v = kWeq[bb] * (rho[j] - rho_ref);
+            else
+                v = feq(bb, rho[j], ux ? ux[j] : 0.0, uy ? uy[j] : 0.0) - kWeq[bb] * rho_ref;
+            out[b] = (T)v;
         }
         store_node<T>(f, g, x, y, out);
     }
+    if (invalid) atomicOr(&bad[lat], 1u);
 }
 
 // Pulled distribution of node (x, y) as FP64 full populations; false if solid.
@@ -80,28 +88,36 @@ __device__ __forceinline__ double psi_fp64(double rho, const Phys<double>& P) {
     return psi_of(rho, P, unused);
 }
 
+// Read-out, pass 1: for every cell with x in [-1, nx], y in [-1, ny] (the
+// nodes and the ghost cells next to them) the pulled distribution gives rho
+// and psi (Eq. 13) in FP64; psi goes to a plane in the ghosted layout
+// (-1 at solid cells), rho and the momentum sum_a e_a f_a of the nodes to
+// the output arrays.
 template <typename T>
-__global__ void moments_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
-                               int lat0, const T* __restrict__ f_base,
-                               const uint8_t* __restrict__ mask_base, double* __restrict__ rho_out,
-                               double* __restrict__ ux_out, double* __restrict__ uy_out,
-                               double* __restrict__ p_out) {
+__global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
+                                   int lat0, const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
+                                   double* __restrict__ psi_base, double* __restrict__ rho_out,
+                                   double* __restrict__ jx_out, double* __restrict__ jy_out) {
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const Phys<double> P = phys[lat];
     const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
     const T* f = f_base + g.f_off;
-    const long long n = (long long)g.nx * g.ny;
+    double* psi_plane = psi_base + g.f_off / 9;  // one plane per lattice, same indexing
+    const long long w = g.nx + 2, n = w * (g.ny + 2);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long o = g.node_off + i;
-        const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+        const int x = (int)(i % w) - 1, y = (int)(i / w) - 1;
         double fc[9];
+        const int c = node_index(g, x, y);
         if (!pulled_fp64<T>(g, f, mask, P.rho_ref, x, y, fc)) {
-            if (rho_out) rho_out[o] = 0.0;
-            if (ux_out) ux_out[o] = 0.0;
-            if (uy_out) uy_out[o] = 0.0;
-            if (p_out) p_out[o] = 0.0;
+            psi_plane[c] = -1.0;
+            if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+                const long long o = g.node_off + (long long)y * g.nx + x;
+                rho_out[o] = 0.0;
+                jx_out[o] = 0.0;
+                jy_out[o] = 0.0;
+            }
             continue;
         }
         double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -110,27 +126,53 @@ __global__ void moments_kernel(const Geom* __restrict__ geoms, const Phys<double
             jx += kEx[a] * fc[a];
             jy += kEy[a] * fc[a];
         }
-        const double psi = psi_fp64(rho, P);
+        psi_plane[c] = psi_fp64(rho, P);
+        if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+            const long long o = g.node_off + (long long)y * g.nx + x;
+            rho_out[o] = rho;
+            jx_out[o] = jx;
+            jy_out[o] = jy;
+        }
+    }
+}
+
+// Read-out, pass 2: force (Eq. 7, a solid neighbour takes the node's psi),
+// velocity (Eq. 6) and pressure (Eq. 10) of every node; ux/uy hold the
+// momentum on entry and the velocity on exit.
+__global__ void moments_force_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
+                                     int lat0, const double* __restrict__ psi_base, const double* __restrict__ rho,
+                                     double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ p) {
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    const Phys<double> P = phys[lat];
+    const double* psi_plane = psi_base + g.f_off / 9;
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+        const long long o = g.node_off + i;
+        const int c = node_index(g, x, y);
+        const double psi = psi_plane[c];
+        if (psi < 0.0) {  // solid node
+            ux[o] = 0.0;
+            uy[o] = 0.0;
+            p[o] = 0.0;
+            continue;
+        }
         double gx = 0.0, gy = 0.0;
         for (int a = 1; a < 9; ++a) {
-            const int xn = x + kEx[a], yn = y + kEy[a];  // ghost frame covers -1 and n
-            double fn[9];
-            double pn = psi;  // solid neighbour: the node's own psi
-            if (pulled_fp64<T>(g, f, mask, P.rho_ref, xn, yn, fn)) {
-                double rn = 0.0;
-                for (int b = 0; b < 9; ++b) rn += fn[b];
-                pn = psi_fp64(rn, P);
-            }
-            const double w = (a < 5) ? (1.0 / 3.0) : (1.0 / 12.0);
-            gx += w * pn * kEx[a];
-            gy += w * pn * kEy[a];
+            double pn = psi_plane[c + kEy[a] * g.pitch + kEx[a]];
+            pn = pn < 0.0 ? psi : pn;
+            const double wa = (a < 5) ? (1.0 / 3.0) : (1.0 / 12.0);
+            gx += wa * pn * kEx[a];
+            gy += wa * pn * kEy[a];
         }
         const double Fx = -P.G * psi * gx, Fy = -P.G * psi * gy;
-        if (rho_out) rho_out[o] = rho;
-        if (ux_out) ux_out[o] = (jx + 0.5 * Fx) / rho;
-        if (uy_out) uy_out[o] = (jy + 0.5 * Fy) / rho;
+        const double r = rho[o];
+        ux[o] = (ux[o] + 0.5 * Fx) / r;
+        uy[o] = (uy[o] + 0.5 * Fy) / r;
         // Eq. 10: p = rho c_s^2 + G c^2 psi^2 / 2
-        if (p_out) p_out[o] = rho * P.cs2 + 0.5 * P.G * psi * psi;
+        p[o] = r * P.cs2 + 0.5 * P.G * psi * psi;
     }
 }
 
@@ -195,17 +237,22 @@ dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
 
 template <typename T>
 cudaError_t init_impl(const LaunchSet& L, const double* rho, const double* ux, const double* uy,
-                      T* f, cudaStream_t s) {
+                      T* f, unsigned* bad, cudaStream_t s) {
     init_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(
-        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f);
+        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t moments_impl(const LaunchSet& L, const T* f, double* rho, double* ux, double* uy,
+cudaError_t moments_impl(const LaunchSet& L, const T* f, double* psi, double* rho, double* ux, double* uy,
                          double* p, cudaStream_t s) {
-    moments_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 128), 128, 0, s>>>(
-        L.geoms, L.phys, L.lat0, f, L.mask, rho, ux, uy, p);
+    // cells of the nodes plus a one-cell frame: (nx + 2)(ny + 2) <= nodes + 2(nx + ny) + 4
+    moments_psi_kernel<T><<<lattice_grid(L.max_nodes + 2 * L.max_extent + 4, L.n_lat, 128), 128, 0, s>>>(
+        L.geoms, L.phys, L.lat0, f, L.mask, psi, rho, ux, uy);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    moments_force_kernel<<<lattice_grid(L.max_nodes, L.n_lat, 128), 128, 0, s>>>(L.geoms, L.phys, L.lat0, psi,
+                                                                                 rho, ux, uy, p);
     return cudaGetLastError();
 }
 
@@ -235,20 +282,20 @@ cudaError_t launch_ghost_refresh_f64(const LaunchSet& L, double* f, cudaStream_t
 }
 
 cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, float* f, cudaStream_t s) {
-    return init_impl<float>(L, rho, ux, uy, f, s);
+                            const double* uy, float* f, unsigned* bad, cudaStream_t s) {
+    return init_impl<float>(L, rho, ux, uy, f, bad, s);
 }
 cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, double* f, cudaStream_t s) {
-    return init_impl<double>(L, rho, ux, uy, f, s);
+                            const double* uy, double* f, unsigned* bad, cudaStream_t s) {
+    return init_impl<double>(L, rho, ux, uy, f, bad, s);
 }
-cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* rho, double* ux,
+cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s) {
-    return moments_impl<float>(L, f, rho, ux, uy, p, s);
+    return moments_impl<float>(L, f, psi, rho, ux, uy, p, s);
 }
-cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* rho, double* ux,
+cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s) {
-    return moments_impl<double>(L, f, rho, ux, uy, p, s);
+    return moments_impl<double>(L, f, psi, rho, ux, uy, p, s);
 }
 cudaError_t launch_mass_f32(const Geom& g, double rho_ref, long long n_fluid, const float* f,
                             const uint8_t* mask, double* partials, double* out, cudaStream_t s) {

@@ -63,21 +63,23 @@ struct LaunchSet {
     const uint8_t* mask;        // device mask base (lattice rows at geom.mask_off)
     int lat0, n_lat;
     long long max_nodes;        // largest nx*ny among the lattices
+    long long max_extent;       // largest nx + ny among the lattices
 };
 
 // Initial state: f_a such that the next pull gathers f_eq(rho, u) at every
 // fluid node. rho/ux/uy are device arrays indexed by geom.node_off + y*nx + x
-// (ux/uy may be null for u = 0).
+// (ux/uy may be null for u = 0). bad[lat] is set to 1 for invalid input.
 cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, float* f, cudaStream_t s);
+                            const double* uy, float* f, unsigned* bad, cudaStream_t s);
 cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, double* f, cudaStream_t s);
+                            const double* uy, double* f, unsigned* bad, cudaStream_t s);
 
 // rho, v (Eq. 6), p (Eq. 10) into device arrays indexed like the init inputs
-// (any may be null), computed in FP64 from the stored distribution.
-cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* rho, double* ux,
+// (all four required), computed in FP64 from the stored distribution; psi is
+// scratch of one ghosted plane per lattice (element offset f_off / 9).
+cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s);
-cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* rho, double* ux,
+cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s);
 
 // Rewrite the ghost frames of lattices [lat0, lat0 + n_lat) from their nodes.
