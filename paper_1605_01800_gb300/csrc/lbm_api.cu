@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -86,6 +87,14 @@ struct lbm_ctx {
     static constexpr int kMaxTma = 8;
     TmaMaps* h_maps[kMaxTma][2] = {};   // host copies passed at launch, by source buffer
     int tma_grid[kMaxTma] = {};
+    // Clock cycles a TMA-variant mbarrier wait may take (about one second),
+    // and bytes added to every stage's expected count (0). The environment
+    // variables LBM_TMA_WAIT_CYCLES and LBM_TMA_EXTRA_TX, read when the context
+    // is created, override them: a test sets a short limit and a few extra
+    // bytes, so that the waits run out (their phase never completes, while
+    // every copy does land) and the step reports LBM_ETIMEOUT without a fault.
+    long long tma_wait_limit = 2000000000LL;
+    unsigned tma_extra_tx = 0;
     int tile_index = 0;
     bool has_tiny = false;       // a lattice under 4 cells in x or y (see launch_one_step)
     unsigned* d_status = nullptr;
@@ -322,7 +331,8 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
     } else if (c->tile_index >= kTileCount) {
         const int v = c->tile_index - kTileCount;
-        TmaArgs a{c->d_tiles, c->n_tiles, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status};
+        TmaArgs a{c->d_tiles, c->n_tiles, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status,
+                  c->tma_wait_limit, c->tma_extra_tx};
         e = launch_step_tma(v, c->tma_grid[v], a, *c->h_maps[v][src], *c->h_table, c->stream);
     } else {
         StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
@@ -504,6 +514,8 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     }
 
     lbm_ctx* c = new lbm_ctx();
+    if (const char* w = getenv("LBM_TMA_WAIT_CYCLES")) c->tma_wait_limit = std::max(0LL, atoll(w));
+    if (const char* x = getenv("LBM_TMA_EXTRA_TX")) c->tma_extra_tx = (unsigned)std::min(4096LL, std::max(0LL, atoll(x)));
     c->n = n;
     c->precision = precision;
     c->elem = precision == LBM_FP64 ? 8 : 4;

@@ -32,6 +32,8 @@ struct TmaArgs {
     const Phys<float>* phys;
     float* fout;               // buffer written this step (whole array)
     unsigned* status;
+    long long wait_limit;      // clock cycles an mbarrier wait may take before the CTA gives up
+    unsigned extra_tx;         // bytes added to every stage's expected count (0; tests only)
 };
 // Tensor maps travel as __grid_constant__ kernel parameters: per lattice the
 // map of the buffer read this step and the map of its wall mask.

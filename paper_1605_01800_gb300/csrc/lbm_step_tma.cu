@@ -88,7 +88,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-constexpr long long kWaitLimit = 2000000000LL;  // clock cycles, about one second
 
 // e_a and the opposite population, as compile-time tables for the gathers
 __device__ __forceinline__ constexpr int ex_of(int a) {
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
         const Tile tl = A.tiles[t];
         const int has_mask = A.geom[tl.lat].has_mask;
         unsigned char* st = smem + s * B::STAGE_BYTES;
-        mbar_arrive_expect_tx(&bars[s], 9 * B::BOX_BYTES + (has_mask ? B::MASK_BYTES : 0));
+        mbar_arrive_expect_tx(&bars[s], 9 * B::BOX_BYTES + (has_mask ? B::MASK_BYTES : 0) + A.extra_tx);
         const CUtensorMap* fm = &M.f[tl.lat];
         const int bx = tl.x0 + kGX - 4, by = tl.y0 + kGY - 2;
 #pragma unroll
@@ -160,7 +159,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
     for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x, ++k) {
         const int s = k % S;
         const uint32_t parity = (uint32_t)((k / S) & 1);
-        const bool ok = mbar_wait_bounded(&bars[s], parity, kWaitLimit);
+        const bool ok = mbar_wait_bounded(&bars[s], parity, A.wait_limit);
         if (__syncthreads_or(!ok)) {
             failed = true;
             if (tid == 0) atomicOr(&A.status[A.tiles[t].lat], FLAG_TIMEOUT);
@@ -254,11 +253,14 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
     }
 
     if (failed && tid == 0) {
-        // wait (bounded) for the loads still in flight into this CTA's stages
+        // wait (bounded) for the loads still in flight into this CTA's stages;
+        // copies land within microseconds, so 50 ms is ample even when the
+        // waits above were shortened
+        const long long drain = A.wait_limit > 100000000LL ? A.wait_limit : 100000000LL;
         for (int j = 0; j < S; ++j) {
             const int kk = k + j;
             const int t = blockIdx.x + kk * gridDim.x;
-            if (t < A.n_tiles) mbar_wait_bounded(&bars[kk % S], (uint32_t)((kk / S) & 1), kWaitLimit);
+            if (t < A.n_tiles) mbar_wait_bounded(&bars[kk % S], (uint32_t)((kk / S) & 1), drain);
         }
     }
 }

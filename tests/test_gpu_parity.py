@@ -287,3 +287,32 @@ def test_coexistence_batch_20000_steps_fp32_vs_fp64():
         assert liq < 1e-4, (i, liq)
         assert vap < (1e-4 if spec.meta["T_over_Tc"] >= 0.55 else 2.5e-4), (i, vap)
         assert rel_err(r32, r64) < 3e-3, i
+
+
+def test_tma_wait_timeout_reports_etimeout_and_context_recovers(monkeypatch):
+    """Failure detection without a GPU fault: every stage expects 16 bytes
+    more than its copies deliver, so its mbarrier phase never completes (the
+    copies themselves all land); the bounded waits (here ~1 ms) run out, each
+    CTA records the timeout, waits for its copies and returns, and the host
+    reports LBM_ETIMEOUT. A context with the normal settings then steps
+    correctly."""
+    specs = [small_spec(64, 40, seed=21)]
+    tma = [t for t in range(lbm.lbm_tile_count()) if t >= 9]
+    if not tma:
+        pytest.skip("no TMA variants")
+    monkeypatch.setenv("LBM_TMA_WAIT_CYCLES", "2000000")
+    monkeypatch.setenv("LBM_TMA_EXTRA_TX", "16")
+    b = lbm.Batch(specs, "fp32_dev")
+    monkeypatch.delenv("LBM_TMA_WAIT_CYCLES")
+    monkeypatch.delenv("LBM_TMA_EXTRA_TX")
+    lbm.lbm_set_tile(b.ctx, tma[0])
+    b.init()
+    b.step(3)
+    rc = lbm.load().lbm_sync(b.ctx)
+    assert rc == lbm.LBM_ETIMEOUT
+    assert b.status(0) & lbm.LBM_FLAG_TIMEOUT
+    b.close()
+    (ok,) = run_gpu(specs, "fp32_dev", 3, tile=tma[0])
+    (ref,) = run_gpu(specs, "fp32_dev", 3, tile=0)
+    for x, y in zip(ok, ref):
+        assert np.array_equal(x, y)
