@@ -10,12 +10,13 @@
 namespace lbm {
 
 // CTA shapes of the step kernel: {TX threads in x, TYT threads in y, RY nodes
-// per thread in y}; the node tile is TX x (TYT * RY). Every shape computes
-// bitwise the same result; they differ only in speed.
+// per thread in y, minimum resident CTAs per SM}; the node tile is
+// TX x (TYT * RY). Every shape computes bitwise the same result; they differ
+// only in speed.
 constexpr int kTileCount = 9;
-constexpr int kTiles[kTileCount][3] = {
-    {32, 8, 2}, {32, 8, 1}, {64, 4, 2}, {64, 4, 1}, {32, 16, 1},
-    {32, 4, 2}, {32, 8, 4}, {64, 8, 1}, {128, 2, 2},
+constexpr int kTiles[kTileCount][4] = {
+    {32, 8, 2, 4}, {32, 4, 2, 7}, {64, 4, 2, 4}, {32, 4, 4, 5}, {32, 2, 4, 10},
+    {32, 4, 2, 8}, {32, 8, 4, 1}, {64, 2, 4, 5}, {128, 2, 2, 4},
 };
 
 template <typename T>

@@ -46,8 +46,6 @@ struct StepArgs {
     unsigned* status;
 };
 
-// Register cap for the FP32 kernel with up to two nodes per thread: 64 per
-// thread, so that 1024 threads per SM are resident.
 // ---- FP32 node math shared by the plain-load and the TMA kernels: nodes are
 // processed in pairs (paired FP32 instructions) when a thread owns an even
 // number of them, one at a time otherwise, with bitwise equal results.
@@ -187,8 +185,10 @@ __device__ __forceinline__ void f32_collide_store(float (&f)[RY][9], const bool 
     }
 }
 
-template <typename T, int TX, int TYT, int RY, bool TABLE>
-__global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 && RY <= 2) ? 1024 / (TX * TYT) : 1)
+// MINB: minimum resident CTAs per SM the register allocation must allow
+// (the register cap is 65536 / (MINB * TX * TYT) per thread).
+template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE>
+__global__ void __launch_bounds__(TX * TYT, MINB)
     step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT) {
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;

@@ -4,12 +4,12 @@
 
 namespace lbm {
 
-template <int TX, int TYT, int RY, bool TABLE>
+template <int TX, int TYT, int RY, int MINB, bool TABLE>
 static cudaError_t launch_tile(int n_tiles, const StepArgs<float>& a, const PhysTable<float>* table,
                                cudaStream_t s) {
     TableOf<float, TABLE> t{};
     if constexpr (TABLE) t = *table;
-    step_kernel<float, TX, TYT, RY, TABLE><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, t);
+    step_kernel<float, TX, TYT, RY, MINB, TABLE><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, t);
     return cudaGetLastError();
 }
 
@@ -17,24 +17,24 @@ cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& 
                             const PhysTable<float>* table, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     switch (tile_index) {
-    case 0: return table ? launch_tile<32, 8, 2, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 8, 2, false>(n_tiles, args, nullptr, s);
-    case 1: return table ? launch_tile<32, 8, 1, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 8, 1, false>(n_tiles, args, nullptr, s);
-    case 2: return table ? launch_tile<64, 4, 2, true>(n_tiles, args, table, s)
-                   : launch_tile<64, 4, 2, false>(n_tiles, args, nullptr, s);
-    case 3: return table ? launch_tile<64, 4, 1, true>(n_tiles, args, table, s)
-                   : launch_tile<64, 4, 1, false>(n_tiles, args, nullptr, s);
-    case 4: return table ? launch_tile<32, 16, 1, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 16, 1, false>(n_tiles, args, nullptr, s);
-    case 5: return table ? launch_tile<32, 4, 2, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 4, 2, false>(n_tiles, args, nullptr, s);
-    case 6: return table ? launch_tile<32, 8, 4, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 8, 4, false>(n_tiles, args, nullptr, s);
-    case 7: return table ? launch_tile<64, 8, 1, true>(n_tiles, args, table, s)
-                   : launch_tile<64, 8, 1, false>(n_tiles, args, nullptr, s);
-    case 8: return table ? launch_tile<128, 2, 2, true>(n_tiles, args, table, s)
-                   : launch_tile<128, 2, 2, false>(n_tiles, args, nullptr, s);
+    case 0: return table ? launch_tile<32, 8, 2, 4, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 8, 2, 4, false>(n_tiles, args, nullptr, s);
+    case 1: return table ? launch_tile<32, 4, 2, 7, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 4, 2, 7, false>(n_tiles, args, nullptr, s);
+    case 2: return table ? launch_tile<64, 4, 2, 4, true>(n_tiles, args, table, s)
+                   : launch_tile<64, 4, 2, 4, false>(n_tiles, args, nullptr, s);
+    case 3: return table ? launch_tile<32, 4, 4, 5, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 4, 4, 5, false>(n_tiles, args, nullptr, s);
+    case 4: return table ? launch_tile<32, 2, 4, 10, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 2, 4, 10, false>(n_tiles, args, nullptr, s);
+    case 5: return table ? launch_tile<32, 4, 2, 8, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 4, 2, 8, false>(n_tiles, args, nullptr, s);
+    case 6: return table ? launch_tile<32, 8, 4, 1, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 8, 4, 1, false>(n_tiles, args, nullptr, s);
+    case 7: return table ? launch_tile<64, 2, 4, 5, true>(n_tiles, args, table, s)
+                   : launch_tile<64, 2, 4, 5, false>(n_tiles, args, nullptr, s);
+    case 8: return table ? launch_tile<128, 2, 2, 4, true>(n_tiles, args, table, s)
+                   : launch_tile<128, 2, 2, 4, false>(n_tiles, args, nullptr, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -6,7 +6,7 @@ namespace lbm {
 
 template <int TX, int TYT, int RY>
 static cudaError_t launch_tile(int n_tiles, const StepArgs<double>& a, cudaStream_t s) {
-    step_kernel<double, TX, TYT, RY, false><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, NoTable{0});
+    step_kernel<double, TX, TYT, RY, 1, false><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, NoTable{0});
     return cudaGetLastError();
 }
 
@@ -14,13 +14,13 @@ cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>&
     if (n_tiles <= 0) return cudaSuccess;
     switch (tile_index) {
     case 0: return launch_tile<32, 8, 2>(n_tiles, args, s);
-    case 1: return launch_tile<32, 8, 1>(n_tiles, args, s);
+    case 1: return launch_tile<32, 4, 2>(n_tiles, args, s);
     case 2: return launch_tile<64, 4, 2>(n_tiles, args, s);
-    case 3: return launch_tile<64, 4, 1>(n_tiles, args, s);
-    case 4: return launch_tile<32, 16, 1>(n_tiles, args, s);
+    case 3: return launch_tile<32, 4, 4>(n_tiles, args, s);
+    case 4: return launch_tile<32, 2, 4>(n_tiles, args, s);
     case 5: return launch_tile<32, 4, 2>(n_tiles, args, s);
     case 6: return launch_tile<32, 8, 4>(n_tiles, args, s);
-    case 7: return launch_tile<64, 8, 1>(n_tiles, args, s);
+    case 7: return launch_tile<64, 2, 4>(n_tiles, args, s);
     case 8: return launch_tile<128, 2, 2>(n_tiles, args, s);
     default: return cudaErrorInvalidValue;
     }
