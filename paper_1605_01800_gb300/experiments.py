@@ -1,0 +1,244 @@
+"""The paper's static-bubble experiments (arXiv:1605.01800, Sec. 3.1-3.2) on the GPU path.
+
+- ``bubble_batch``: static vapour bubbles (Eq. 16 with vapour inside) of several
+  radii on periodic square lattices, one batch.
+- ``laplace_fit``: runs a batch through the C ABI and fits the Laplace law,
+  Eq. 17, |p_out - p_in| = sigma / r, with r the equivalent radius of the
+  vapour area and p of Eq. 10 averaged inside the bubble and in the far liquid.
+
+Eq. 17 is printed as p_out - p_in = sigma / r; a bubble's inside pressure is
+the higher one, so the fit uses the magnitude. The coexistence densities the
+bubbles start from are those of ``cs_coexistence.json``; for fixed b and T/Tc
+they do not depend on a (p_EOS scales with a at fixed T/Tc), only T_c does.
+"""
+from typing import List, Sequence
+
+import numpy as np
+
+from . import inputs, lbm
+
+
+def bubble_batch(radii: Sequence[float], t_over_tc: float, a: float = 1.0, n: int = 201,
+                 tau_nu: float = 0.6, eps: float = 1.86, width: float = 5.0) -> List[inputs.LatticeSpec]:
+    c = inputs.coexistence(t_over_tc)
+    T = t_over_tc * inputs.critical_temperature() * a  # T_c is proportional to a
+    specs = []
+    for R in radii:
+        rho = inputs.tanh_profile(n, n, (n - 1) / 2, (n - 1) / 2, R, c["rho_l"], c["rho_g"], width)
+        specs.append(inputs.LatticeSpec(n, n, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=c["rho_g"],
+                                        a=a, b=4.0, meta={"R0": R, "rho_l": c["rho_l"], "rho_g": c["rho_g"]}))
+    return specs
+
+
+def measure_bubbles(batch: "lbm.Batch") -> List[dict]:
+    """Equivalent radius, inside/outside density and pressure of each bubble.
+    Pressures are averaged over the inner half of the bubble and over the
+    liquid more than 15 nodes outside its interface, which removes most of
+    the node-to-node oscillation of p near a sharp interface."""
+    out = []
+    for i, s in enumerate(batch.specs):
+        rho, ux, uy, p = batch.moments(i, allow_flags=True)
+        cy, cx = s.ny // 2, s.nx // 2
+        rin, rout = rho[cy, cx], rho[0, 0]
+        frac = np.clip((rout - rho) / (rout - rin), 0.0, 1.0)
+        r_eq = float(np.sqrt(frac.sum() / np.pi))
+        yy, xx = np.mgrid[0:s.ny, 0:s.nx]
+        d = np.hypot(xx - (s.nx - 1) / 2, yy - (s.ny - 1) / 2)
+        inner, outer = d < 0.5 * r_eq, d > r_eq + 15.0
+        out.append({"R0": s.meta["R0"], "r": r_eq, "rho_in": float(rho[inner].mean()),
+                    "rho_out": float(rho[outer].mean()), "p_in": float(p[inner].mean()),
+                    "p_out": float(p[outer].mean()),
+                    "umax": float(max(np.abs(ux).max(), np.abs(uy).max())), "status": batch.status(i)})
+    return out
+
+
+def laplace_fit(radii: Sequence[float], t_over_tc: float, steps: int, a: float = 1.0, tau_nu: float = 0.6,
+                eps: float = 1.86, n: int = 201, stream=None) -> dict:
+    """Run static bubbles for `steps` steps and fit the Laplace law.
+
+    `sigma` is the least-squares slope of Eq. 17 as written, |dp| = sigma / r
+    (a line through the origin); `sigma_free`, `intercept` and `r2` are the
+    fit |dp| = sigma / r + c, whose small intercept and r2 near 1 show that
+    the bubbles obey the 1/r law."""
+    specs = bubble_batch(radii, t_over_tc, a=a, n=n, tau_nu=tau_nu, eps=eps)
+    b = lbm.Batch(specs, "fp32_dev", stream=stream)
+    b.init()
+    b.step(steps)
+    rows = measure_bubbles(b)
+    b.close()
+    inv_r = np.array([1.0 / r["r"] for r in rows])
+    dp = np.array([abs(r["p_out"] - r["p_in"]) for r in rows])
+    sigma = float(np.dot(inv_r, dp) / np.dot(inv_r, inv_r))
+    A = np.vstack([inv_r, np.ones_like(inv_r)]).T
+    (sigma_free, intercept), *_ = np.linalg.lstsq(A, dp, rcond=None)
+    pred = A @ np.array([sigma_free, intercept])
+    r2 = 1.0 - float(np.sum((dp - pred) ** 2) / np.sum((dp - dp.mean()) ** 2))
+    return {"sigma": sigma, "sigma_free": float(sigma_free), "intercept": float(intercept), "r2": r2,
+            "bubbles": rows}
+
+
+def coexistence_curve(t_over_tc: Sequence[float], eps: Sequence[float], tau_nu: Sequence[float], steps: int,
+                      a: float = 0.5, n: int = 201, r0: float = 70.0, width: float = 5.0, stream=None) -> List[dict]:
+    """Static bubbles of radius r0 (Sec. 3.1, Fig. 1 and 2): one lattice per
+    (T/Tc, eps, tau_nu), all in one batch, run for `steps` steps; returns the
+    vapour density (inner half of the bubble) and the liquid density (more
+    than 15 nodes outside the interface) of each."""
+    combos = [(t, e, tn) for t in t_over_tc for e in eps for tn in tau_nu]
+    specs = []
+    for t, e, tn in combos:
+        specs += bubble_batch([r0], t, a=a, n=n, tau_nu=tn, eps=e, width=width)
+    b = lbm.Batch(specs, "fp32_dev", stream=stream)
+    b.init()
+    b.step(steps)
+    rows = measure_bubbles(b)
+    b.close()
+    out = []
+    for (t, e, tn), r in zip(combos, rows):
+        out.append({"t_over_tc": t, "eps": e, "tau_nu": tn, "rho_g": r["rho_in"], "rho_l": r["rho_out"],
+                    "r": r["r"], "umax": r["umax"], "status": r["status"]})
+    return out
+
+
+# ---------------------------------------------------------------- dynamic cases (Sec. 3.2, Sec. 4)
+
+def inception_spec(n: int = 201, rho_init: float = 0.2609, rel_perturbation: float = 1e-8, t_over_tc: float = 0.5,
+                   a: float = 0.5, tau_nu: float = 0.6, eps: float = 1.86) -> inputs.LatticeSpec:
+    """Homogeneous cavitation inception (Sec. 3.2, Fig. 4): uniform density
+    rho_init inside the spinodal region, raised by rho_init * rel_perturbation
+    on the row (ly - 1) / 2, periodic in x and y."""
+    T = t_over_tc * inputs.critical_temperature() * a
+    rho = np.full((n, n), rho_init)
+    rho[(n - 1) // 2, :] += rho_init * rel_perturbation
+    return inputs.LatticeSpec(n, n, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=rho_init, a=a, b=4.0,
+                              meta={"rho_init": rho_init})
+
+
+def inception_run(steps: int, every: int = 10, precision: str = "fp64", stream=None, **kw) -> dict:
+    """Density histories at the two probes of Fig. 4: the perturbed row's
+    centre ((lx-1)/2, (ly-1)/2) and ((lx-1)/2, ly-1)."""
+    spec = inception_spec(**kw)
+    n = spec.nx
+    b = lbm.Batch([spec], precision, stream=stream)
+    b.init()
+    t, centre, edge, rmin = [0], [], [], []
+    rho = b.moments(0, allow_flags=True)[0]
+    centre.append(float(rho[(n - 1) // 2, (n - 1) // 2]))
+    edge.append(float(rho[n - 1, (n - 1) // 2]))
+    rmin.append(float(rho.min()))
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        b.step(k)
+        done += k
+        rho = b.moments(0, allow_flags=True)[0]
+        t.append(done)
+        centre.append(float(rho[(n - 1) // 2, (n - 1) // 2]))
+        edge.append(float(rho[n - 1, (n - 1) // 2]))
+        rmin.append(float(rho.min()))
+    status = b.status(0)
+    b.close()
+    return {"t": t, "centre": centre, "edge": edge, "min": rmin, "status": status}
+
+
+def vapour_radius(rho: np.ndarray, rho_l: float, rho_g: float) -> float:
+    """Equivalent radius of the vapour area: sqrt(A / pi), A the vapour
+    fraction (rho_l - rho) / (rho_l - rho_g) summed over the nodes."""
+    frac = np.clip((rho_l - rho) / (rho_l - rho_g), 0.0, 1.0)
+    return float(np.sqrt(frac.sum() / np.pi))
+
+
+def nucleus_run(radii: Sequence[float], rho_liquid: float, steps: int, every: int = 1000, n: int = 401,
+                t_over_tc: float = 0.5, a: float = 0.5, tau_nu: float = 0.6, eps: float = 1.86, width: float = 5.0,
+                stream=None) -> List[dict]:
+    """Critical nucleus (Sec. 3.2, Eq. 18, Fig. 5): vapour bubbles of the given
+    radii at the coexistence vapour density, centred in liquid of density
+    rho_liquid on n x n periodic lattices; radius histories r(t)."""
+    c = inputs.coexistence(t_over_tc)
+    T = t_over_tc * inputs.critical_temperature() * a
+    specs = []
+    for R in radii:
+        rho = inputs.tanh_profile(n, n, (n - 1) / 2, (n - 1) / 2, R, rho_liquid, c["rho_g"], width)
+        specs.append(inputs.LatticeSpec(n, n, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=c["rho_g"],
+                                        a=a, b=4.0, meta={"R0": R}))
+    b = lbm.Batch(specs, "fp32_dev", stream=stream)
+    b.init()
+    hist = [[] for _ in radii]
+    done = 0
+    while True:
+        for i in range(len(radii)):
+            hist[i].append(vapour_radius(b.moments(i, allow_flags=True)[0], rho_liquid, c["rho_g"]))
+        if done >= steps:
+            break
+        k = min(every, steps - done)
+        b.step(k)
+        done += k
+    out = [{"R0": R, "r": h, "status": b.status(i)} for i, (R, h) in enumerate(zip(radii, hist))]
+    b.close()
+    return out
+
+
+def wall_collapse_spec(nx: int = 1801, ny: int = 301, R0: float = 138.0, d: float = 150.0,
+                       liquid_factor: float = 1.02, t_over_tc: float = 0.5, a: float = 0.5, tau_nu: float = 0.51,
+                       eps: float = 1.86, width: float = 5.0) -> inputs.LatticeSpec:
+    """Bubble collapse between two parallel walls (Sec. 4.1, Eq. 19-20):
+    solid rows y = 0 and y = ny - 1 (halfway bounce-back), periodic in x, a
+    vapour bubble of radius R0 centred at height d above the lower wall in
+    liquid at liquid_factor times the coexistence density (the overpressure)."""
+    c = inputs.coexistence(t_over_tc)
+    T = t_over_tc * inputs.critical_temperature() * a
+    rho_liq = liquid_factor * c["rho_l"]
+    rho = inputs.tanh_profile(nx, ny, (nx - 1) / 2, d, R0, rho_liq, c["rho_g"], width)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[0, :] = 1
+    solid[ny - 1, :] = 1
+    rho[solid == 1] = rho_liq
+    return inputs.LatticeSpec(nx, ny, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=c["rho_g"], solid=solid,
+                              a=a, b=4.0, meta={"R0": R0, "d": d, "rho_l": rho_liq, "rho_g": c["rho_g"]})
+
+
+def _vapour_components(vap: np.ndarray) -> int:
+    """Number of 4-connected vapour regions (periodic in x)."""
+    from scipy import ndimage
+    lab, k = ndimage.label(vap)
+    if k > 1:  # merge labels that touch across the periodic x boundary
+        parent = list(range(k + 1))
+
+        def find(i):
+            while parent[i] != i:
+                i = parent[i]
+            return i
+        for l0, l1 in zip(lab[:, 0], lab[:, -1]):
+            if l0 and l1:
+                parent[find(l0)] = find(l1)
+        k = len({find(i) for i in range(1, k + 1)})
+    return k
+
+
+def wall_collapse_run(steps: int, every: int = 500, stream=None, **kw) -> dict:
+    """Shape history of the collapsing bubble: vapour area, lateral and
+    vertical extent, number of vapour regions and the largest wall-normal
+    speed, every `every` steps."""
+    spec = wall_collapse_spec(**kw)
+    rl, rg = spec.meta["rho_l"], spec.meta["rho_g"]
+    thr = 0.5 * (rl + rg)
+    b = lbm.Batch([spec], "fp32_dev", stream=stream)
+    b.init()
+    rows = []
+    done = 0
+    while True:
+        rho, ux, uy, _ = b.moments(0, allow_flags=True)
+        vap = (rho < thr) & (spec.solid == 0)
+        ys, xs = np.nonzero(vap)
+        rows.append({"t": done, "area": int(vap.sum()),
+                     "width": int(xs.max() - xs.min() + 1) if xs.size else 0,
+                     "height": int(ys.max() - ys.min() + 1) if ys.size else 0,
+                     "regions": _vapour_components(vap) if xs.size else 0,
+                     "uy_max": float(np.abs(uy).max()), "ux_max": float(np.abs(ux).max())})
+        if done >= steps or not xs.size:
+            break
+        k = min(every, steps - done)
+        b.step(k)
+        done += k
+    status = b.status(0)
+    b.close()
+    return {"history": rows, "status": status}
