@@ -78,33 +78,14 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // psi of Eq. 13 with the CS pressure of Eq. 15, written as
 // psi^2 = kpsi * rho * (R T Z(eta) - a rho - c_s^2), Z = (1+h+h^2-h^3)/(1-h)^3.
 // Near the density where psi^2 = 0 the bracket cancels; the FP32 version
-// recomputes it in FP64 there. psi^2 < 0 is clamped to 0 and flagged.
+// (vpsi below) recomputes it in FP64 there. psi^2 < 0 is clamped to 0 and
+// flagged.
 __device__ __forceinline__ double psi_bracket_fp64(double rho, double RT, double a,
                                                    double b4, double cs2) {
     double eta = b4 * rho;
     double om = 1.0 - eta;
     double num = 1.0 + eta * (1.0 + eta * (1.0 - eta));
     return RT * (num / (om * om * om)) - a * rho - cs2;
-}
-
-// FP32: the quotient and the square root use the fast hardware approximations
-// (about 2 ulp); the state itself is FP32, so they add no visible error.
-__device__ __forceinline__ float psi_of(float rho, const Phys<float>& P, unsigned& flag) {
-    const float eta = P.b4 * rho;
-    const float om = 1.0f - eta;
-    const float num = fmaf(eta, fmaf(eta, 1.0f - eta, 1.0f), 1.0f);
-    float q = fmaf(P.RT, __fdividef(num, om * om * om), -fmaf(P.a, rho, P.cs2));
-    if (fabsf(q) < 0.0078125f * P.cs2)
-        q = (float)psi_bracket_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b4,
-                                    (double)P.cs2);
-    float psi2 = P.kpsi * rho * q;
-    // flags and clamp as selects (no branches): psi^2 < 0 is clamped; NaN,
-    // overflow or a density past close packing (eta >= 1) is non-finite
-    const bool dense_ok = om > 0.0f;
-    flag |= (psi2 < 0.0f && dense_ok) ? FLAG_PSI_CLAMPED : 0u;
-    flag |= (!(psi2 <= 3.0e38f) || !dense_ok) ? FLAG_NONFINITE : 0u;
-    psi2 = (psi2 > 0.0f && dense_ok) ? psi2 : 0.0f;
-    return psi2 > 0.0f ? psi2 * rsqrtf(psi2) : 0.0f;
 }
 
 __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsigned& flag) {
@@ -182,20 +163,16 @@ __device__ __forceinline__ void store_ghost_images(T* __restrict__ base, const G
         }
 }
 
+// The ghost images of node (x, y) at stored index c: for a node within two
+// cells of an edge of a lattice at least 4 x 4, each of x +- nx, y +- ny and
+// the corner combination gets a copy of v (one image per direction at most).
 template <typename T>
-__device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, int x, int y,
-                                           const T v[9]) {
-    const int c = node_index(g, x, y);
-    const int plane = (int)g.plane;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) base[a * plane + c] = v[a];
+__device__ __forceinline__ void store_images(T* __restrict__ base, const Geom& g, int c, int x, int y,
+                                             const T v[9]) {
     const bool ex = x < 2 || x >= g.nx - 2;
     const bool ey = y < 2 || y >= g.ny - 2;
     if (!(ex || ey)) return;
-    // lattices under 4 cells in x or y can have several images per node;
-    // their frames are rewritten by ghost_refresh_kernel after each step
-    if (g.nx < 4 || g.ny < 4) return;
-    // one image per direction at most: x +- nx and y +- ny (offsets in cells)
+    const int plane = (int)g.plane;
     const int dx = !ex ? 0 : (x < 2 ? g.nx : -g.nx);
     const int dy = !ey ? 0 : (y < 2 ? g.ny : -g.ny) * g.pitch;
     if (dx != 0) {
@@ -210,6 +187,19 @@ __device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, 
             for (int a = 0; a < 9; ++a) base[a * plane + c + dx + dy] = v[a];
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, int x, int y,
+                                           const T v[9]) {
+    const int c = node_index(g, x, y);
+    const int plane = (int)g.plane;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) base[a * plane + c] = v[a];
+    // lattices under 4 cells in x or y can have several images per node;
+    // their frames are rewritten by ghost_refresh_kernel after each step
+    if (g.nx < 4 || g.ny < 4) return;
+    store_images<T>(base, g, c, x, y, v);
 }
 
 // Sum of the eight moving populations in a fixed association; the density
@@ -364,9 +354,19 @@ __device__ __forceinline__ V vsum9(const V f[9]) {
     return f[0] + vsum8(f);
 }
 
+// Square root by the hardware approximation (sqrt.approx, relative error
+// about 2^-23; subnormal inputs flush to zero).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // psi of Eq. 13 (see psi_of above): the polynomial in explicit operations, the
-// quotient and square root per lane with the fast hardware approximations,
-// the FP64 fallback near the psi = 0 root and the flags per lane.
+// quotient per lane with the fast hardware approximation, the FP64 fallback
+// near the psi = 0 root, and per lane one combined test of the three
+// conditions that need a flag (psi^2 < 0, non-finite, eta >= 1), whose rare
+// failure is sorted out off the common path.
 template <class V>
 __device__ __forceinline__ V vpsi(V rho, const Phys<float>& P, unsigned& flag) {
     const V one = splat<V>(1.0f);
@@ -380,16 +380,16 @@ __device__ __forceinline__ V vpsi(V rho, const Phys<float>& P, unsigned& flag) {
 #pragma unroll
     for (int i = 0; i < lanes(V{}); ++i) {
         float p2 = lane(psi2, i);
-        const float qi = lane(q, i), ri = lane(rho, i);
+        const float qi = lane(q, i), ri = lane(rho, i), omi = lane(om, i);
         if (fabsf(qi) < 0.0078125f * P.cs2)
             p2 = __fmul_rn(__fmul_rn(P.kpsi, ri),
                            (float)psi_bracket_fp64((double)ri, (double)P.RT, (double)P.a, (double)P.b4,
                                                    (double)P.cs2));
-        const bool dense_ok = lane(om, i) > 0.0f;
-        flag |= (p2 < 0.0f && dense_ok) ? FLAG_PSI_CLAMPED : 0u;
-        flag |= (!(p2 <= 3.0e38f) || !dense_ok) ? FLAG_NONFINITE : 0u;
-        p2 = (p2 > 0.0f && dense_ok) ? p2 : 0.0f;
-        set_lane(out, i, p2 > 0.0f ? __fmul_rn(p2, rsqrtf(p2)) : 0.0f);
+        if (!(p2 >= 0.0f && p2 <= 3.0e38f && omi > 0.0f)) {
+            flag |= (p2 < 0.0f && omi > 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
+            p2 = 0.0f;
+        }
+        set_lane(out, i, sqrt_approx(p2));
     }
     return out;
 }

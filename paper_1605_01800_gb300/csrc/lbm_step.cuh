@@ -185,28 +185,139 @@ __device__ __forceinline__ void f32_collide_store(float (&f)[RY][9], const bool 
     }
 }
 
-// MINB: minimum resident CTAs per SM the register allocation must allow
-// (the register cap is 65536 / (MINB * TX * TYT) per thread).
-template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE>
-__global__ void __launch_bounds__(TX * TYT, MINB)
-    step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT) {
+// ---- FP32 fast path: a tile that lies wholly inside a lattice of at least
+// 4 x 4 nodes without walls. Every own node and halo cell exists, so there
+// are no liveness tests; a thread's nodes stay in register pairs (F2) from
+// the loads to the stores, and the ghost images are written only by tiles
+// within two cells of an edge. The arithmetic is that of the general path
+// operation for operation, so both give bitwise the same result.
+
+// the nine pulled populations of the vertically adjacent nodes at stored
+// indices c and c + pitch, as pairs (no walls)
+__device__ __forceinline__ void pull_pair(const float* __restrict__ fin, int plane, int pitch, int c, F2 f[9]) {
+    auto ld2 = [&](int i) { return F2{make_float2(fin[i], fin[i + pitch])}; };
+    f[0] = ld2(c);
+    f[1] = ld2(1 * plane + c - 1);
+    f[2] = ld2(2 * plane + c - pitch);
+    f[3] = ld2(3 * plane + c + 1);
+    f[4] = ld2(4 * plane + c + pitch);
+    f[5] = ld2(5 * plane + c - pitch - 1);
+    f[6] = ld2(6 * plane + c - pitch + 1);
+    f[7] = ld2(7 * plane + c + pitch + 1);
+    f[8] = ld2(8 * plane + c + pitch - 1);
+}
+
+template <int TX, int TYT, int RY>
+__device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Tile& tile, const Geom& g,
+                                              const Phys<float>& P, float* s_psi) {
+    static_assert(RY % 2 == 0, "the fast path pairs nodes");
+    constexpr int TY = TYT * RY;
+    constexpr int SW = TX + 2;
+    constexpr int SH = TY + 2;
+    constexpr int NT = TX * TYT;
+    constexpr int NH = 2 * SW + 2 * TY;
+    constexpr int NHT = (NH + NT - 1) / NT;
+    constexpr int NP = RY / 2;
+    const float* __restrict__ fin = A.fin + g.f_off;
+    const int plane = (int)g.plane, pitch = g.pitch;
+    const float rho_ref = P.rho_ref;
+    unsigned flag = 0;
+    const int lx = threadIdx.x, ly0 = threadIdx.y * RY;
+    const int x = tile.x0 + lx, y0 = tile.y0 + ly0;
+    const int c0 = node_index(g, x, y0);
+
+    F2 f[NP][9];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) pull_pair(fin, plane, pitch, c0 + 2 * p * pitch, f[p]);
+
+    // halo ring: psi only
+    float ph[NHT];
+    int hc[NHT];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < NHT; ++k) {
+        const int h = tid + k * NT;
+        hc[k] = -1;
+        if (h < NH) {
+            int cx, cy;
+            if (h < SW) {
+                cx = h;
+                cy = 0;
+            } else if (h < 2 * SW) {
+                cx = h - SW;
+                cy = SH - 1;
+            } else {
+                const int q = h - 2 * SW;
+                cy = 1 + (q >> 1);
+                cx = (q & 1) ? SW - 1 : 0;
+            }
+            hc[k] = cy * SW + cx;
+            float fh[9];
+            pull_node<float>(fin, nullptr, plane, pitch, node_index(g, tile.x0 - 1 + cx, tile.y0 - 1 + cy), fh);
+            ph[k] = f32_halo_psi(fh, rho_ref, P, flag);
+        }
+    }
+
+    // own nodes: density and psi
+    F2 drho[NP], rho[NP], psi[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        drho[p] = vsum9(f[p]);
+        rho[p] = splat<F2>(rho_ref) + drho[p];
+        psi[p] = vpsi(rho[p], P, flag);
+        s_psi[(ly0 + 2 * p + 1) * SW + lx + 1] = psi[p].v.x;
+        s_psi[(ly0 + 2 * p + 2) * SW + lx + 1] = psi[p].v.y;
+    }
+#pragma unroll
+    for (int k = 0; k < NHT; ++k)
+        if (hc[k] >= 0) s_psi[hc[k]] = ph[k];
+    __syncthreads();
+    if (flag) atomicOr(&A.status[tile.lat], flag);
+
+    float* __restrict__ fo = A.fout + g.f_off;
+    const bool edge = tile.x0 < 2 || tile.x0 + TX > g.nx - 2 || tile.y0 < 2 || tile.y0 + TY > g.ny - 2;
+    const F2 mG = splat<F2>(-P.G);
+    const F2 G2 = splat<F2>(__fmul_rn(P.G, P.G));
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        // force, Eq. 7, from the psi tile (row stride SW)
+        const int c = (ly0 + 2 * p + 1) * SW + lx + 1;
+        auto nb2 = [&](int o) { return F2{make_float2(s_psi[c + o], s_psi[c + SW + o])}; };
+        F2 gx, gy;
+        vforce_sum(nb2(1), nb2(SW), nb2(-1), nb2(-SW), nb2(SW + 1), nb2(SW - 1), nb2(-SW - 1), nb2(-SW + 1), gx, gy);
+        const F2 mGpsi = mG * psi[p];
+        const F2 Fx = mGpsi * gx, Fy = mGpsi * gy;
+        const F2 g2G2 = G2 * vfma(gx, gx, gy * gy);
+        // collision, Eq. 3, and the store of f*
+        vcollide(f[p], rho[p], drho[p], Fx, Fy, g2G2, P);
+        const int cs = c0 + 2 * p * pitch;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            fo[a * plane + cs] = f[p][a].v.x;
+            fo[a * plane + cs + pitch] = f[p][a].v.y;
+        }
+        if (edge) {
+            float v0[9], v1[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                v0[a] = f[p][a].v.x;
+                v1[a] = f[p][a].v.y;
+            }
+            store_images<float>(fo, g, cs, x, y0 + 2 * p, v0);
+            store_images<float>(fo, g, cs + pitch, x, y0 + 2 * p + 1, v1);
+        }
+    }
+}
+
+// One tile by the general path (any tile: partial, walled, tiny lattices).
+template <typename T, int TX, int TYT, int RY>
+__device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& tile, const Geom& g,
+                                             const Phys<T>& P, T* s_psi) {
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
     constexpr int NT = TX * TYT;
     constexpr int NH = 2 * SW + 2 * TY;  // halo ring cells
-    __shared__ T s_psi[SH * SW];
-
-    const Tile tile = A.tiles[blockIdx.x];
-    const Geom g = A.geom[tile.lat];
-    // restrict: the stores to fout cannot alias the parameters, so they need
-    // not be reloaded after every store
-    const Phys<T>* __restrict__ Pp;
-    if constexpr (TABLE)
-        Pp = &PT.p[tile.lat];
-    else
-        Pp = A.phys + tile.lat;
-    const Phys<T>& P = *Pp;
     const T* __restrict__ fin = A.fin + g.f_off;
     const uint8_t* __restrict__ mask = g.has_mask ? A.mask + g.mask_off : nullptr;
     const int plane = (int)g.plane;
@@ -315,6 +426,36 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
             store_node<T>(fo, g, x, y, f[r]);
         }
     }
+}
+
+// MINB: minimum resident CTAs per SM the register allocation must allow
+// (the register cap is 65536 / (MINB * TX * TYT) per thread). One CTA per
+// tile; full tiles of wall-free lattices take the FP32 fast path.
+template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE>
+__global__ void __launch_bounds__(TX * TYT, MINB)
+    step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT) {
+    constexpr int TY = TYT * RY;
+    constexpr int SW = TX + 2;
+    constexpr int SH = TY + 2;
+    __shared__ T s_psi[SH * SW];
+
+    const Tile tile = A.tiles[blockIdx.x];
+    const Geom g = A.geom[tile.lat];
+    // restrict: the stores to fout cannot alias the parameters, so they need
+    // not be reloaded after every store
+    const Phys<T>* __restrict__ Pp;
+    if constexpr (TABLE)
+        Pp = &PT.p[tile.lat];
+    else
+        Pp = A.phys + tile.lat;
+    const Phys<T>& P = *Pp;
+    if constexpr (std::is_same<T, float>::value && RY % 2 == 0) {
+        if (!g.has_mask && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4) {
+            f32_tile_fast<TX, TYT, RY>(A, tile, g, P, s_psi);
+            return;
+        }
+    }
+    tile_general<T, TX, TYT, RY>(A, tile, g, P, s_psi);
 }
 
 }  // namespace lbm

@@ -45,9 +45,11 @@ def measure_bubbles(batch: "lbm.Batch") -> List[dict]:
         yy, xx = np.mgrid[0:s.ny, 0:s.nx]
         d = np.hypot(xx - (s.nx - 1) / 2, yy - (s.ny - 1) / 2)
         inner, outer = d < 0.5 * r_eq, d > r_eq + 15.0
-        out.append({"R0": s.meta["R0"], "r": r_eq, "rho_in": float(rho[inner].mean()),
-                    "rho_out": float(rho[outer].mean()), "p_in": float(p[inner].mean()),
-                    "p_out": float(p[outer].mean()),
+
+        def mean(a, sel):
+            return float(a[sel].mean()) if sel.any() else float("nan")   # nan: a run that diverged
+        out.append({"R0": s.meta["R0"], "r": r_eq, "rho_in": mean(rho, inner), "rho_out": mean(rho, outer),
+                    "p_in": mean(p, inner), "p_out": mean(p, outer),
                     "umax": float(max(np.abs(ux).max(), np.abs(uy).max())), "status": batch.status(i)})
     return out
 
@@ -101,15 +103,17 @@ def coexistence_curve(t_over_tc: Sequence[float], eps: Sequence[float], tau_nu: 
 
 # ---------------------------------------------------------------- dynamic cases (Sec. 3.2, Sec. 4)
 
-def inception_spec(n: int = 201, rho_init: float = 0.2609, rel_perturbation: float = 1e-8, t_over_tc: float = 0.5,
+def inception_spec(n: int = 201, rho_init: float = 0.2609, rel_perturbation: float = -1e-8, t_over_tc: float = 0.5,
                    a: float = 0.5, tau_nu: float = 0.6, eps: float = 1.86) -> inputs.LatticeSpec:
     """Homogeneous cavitation inception (Sec. 3.2, Fig. 4): uniform density
-    rho_init inside the spinodal region, raised by rho_init * rel_perturbation
-    on the row (ly - 1) / 2, periodic in x and y."""
+    rho_init inside the spinodal region, changed by rho_init * rel_perturbation
+    on the row (ly - 1) / 2, periodic in x and y. The paper gives the size of
+    the perturbation, not its sign; a deficit is the one that makes vapour
+    appear first on that row, as the paper reports."""
     T = t_over_tc * inputs.critical_temperature() * a
     rho = np.full((n, n), rho_init)
     rho[(n - 1) // 2, :] += rho_init * rel_perturbation
-    return inputs.LatticeSpec(n, n, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=rho_init, a=a, b=4.0,
+    return inputs.LatticeSpec(n, n, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=float(rho.min()), a=a, b=4.0,
                               meta={"rho_init": rho_init})
 
 
@@ -141,10 +145,10 @@ def inception_run(steps: int, every: int = 10, precision: str = "fp64", stream=N
 
 
 def vapour_radius(rho: np.ndarray, rho_l: float, rho_g: float) -> float:
-    """Equivalent radius of the vapour area: sqrt(A / pi), A the vapour
-    fraction (rho_l - rho) / (rho_l - rho_g) summed over the nodes."""
-    frac = np.clip((rho_l - rho) / (rho_l - rho_g), 0.0, 1.0)
-    return float(np.sqrt(frac.sum() / np.pi))
+    """Equivalent radius sqrt(A / pi) of the vapour area A: the nodes below
+    the mean of rho_l and rho_g (insensitive to small drifts of the liquid
+    density far from the bubble)."""
+    return float(np.sqrt(np.count_nonzero(rho < 0.5 * (rho_l + rho_g)) / np.pi))
 
 
 def nucleus_run(radii: Sequence[float], rho_liquid: float, steps: int, every: int = 1000, n: int = 401,
@@ -162,19 +166,25 @@ def nucleus_run(radii: Sequence[float], rho_liquid: float, steps: int, every: in
                                         a=a, b=4.0, meta={"R0": R}))
     b = lbm.Batch(specs, "fp32_dev", stream=stream)
     b.init()
-    hist = [[] for _ in radii]
+    hist = [{"R0": R, "t": [], "r": [], "rho_centre": [], "rho_liquid": []} for R in radii]
     done = 0
     while True:
         for i in range(len(radii)):
-            hist[i].append(vapour_radius(b.moments(i, allow_flags=True)[0], rho_liquid, c["rho_g"]))
+            rho = b.moments(i, allow_flags=True)[0]
+            h = hist[i]
+            h["t"].append(done)
+            h["r"].append(vapour_radius(rho, rho_liquid, c["rho_g"]))
+            h["rho_centre"].append(float(rho[(n - 1) // 2, (n - 1) // 2]))
+            h["rho_liquid"].append(float(rho[0, 0]))
         if done >= steps:
             break
         k = min(every, steps - done)
         b.step(k)
         done += k
-    out = [{"R0": R, "r": h, "status": b.status(i)} for i, (R, h) in enumerate(zip(radii, hist))]
+    for i, h in enumerate(hist):
+        h["status"] = b.status(i)
     b.close()
-    return out
+    return hist
 
 
 def wall_collapse_spec(nx: int = 1801, ny: int = 301, R0: float = 138.0, d: float = 150.0,
