@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_step_f32.cu", "lbm_step_f64.cu", "lbm_step_tma.cu", "lbm_aux.cu",
-           "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_step_f32.cu", "lbm_step_f64.cu", "lbm_step_tma.cu", "lbm_step_pipe.cu",
+           "lbm_aux.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

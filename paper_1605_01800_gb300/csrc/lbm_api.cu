@@ -81,7 +81,13 @@ struct lbm_ctx {
     Phys<float>* d_phys_f = nullptr;
     Phys<double>* d_phys_d = nullptr;
     Tile* d_tiles = nullptr;
-    int n_tiles = 0;
+    int n_tiles = 0;             // tiles of the plain (or TMA) kernel
+    // pipelined variants: the full wall-free tiles go to the persistent
+    // kernel (d_fast, n_fast, pipe_grid CTAs), the rest (d_tiles) to the plain
+    // kernel of the same node tile
+    FastTile* d_fast = nullptr;
+    int n_fast = 0;
+    int pipe_grid = 0;
     // TMA variants: tensor maps per variant (box shape) and source buffer,
     // encoded once and passed to every launch as kernel parameters.
     static constexpr int kMaxTma = 8;
@@ -204,6 +210,7 @@ void free_ctx(lbm_ctx* c) {
     delete c->h_table;
     for (int v = 0; v < lbm_ctx::kMaxTma; ++v)
         for (int b = 0; b < 2; ++b) delete c->h_maps[v][b];
+    cudaFree(c->d_fast);
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
     cudaFree(c->d_scalar);
@@ -213,15 +220,30 @@ void free_ctx(lbm_ctx* c) {
     delete c;
 }
 
-int total_tiles() { return kTileCount + tma_variant_count(); }
+int total_tiles() { return kTileCount + tma_variant_count() + pipe_variant_count(); }
+int pipe_first() { return kTileCount + tma_variant_count(); }
+bool is_tma(int index) { return index >= kTileCount && index < pipe_first(); }
+bool is_pipe(int index) { return index >= pipe_first(); }
 
 void tile_shape(int index, int* tx, int* ty) {
     if (index < kTileCount) {
         *tx = kTiles[index][0];
         *ty = kTiles[index][1] * kTiles[index][2];
-    } else {
+    } else if (is_tma(index)) {
         tma_variant_shape(index - kTileCount, tx, ty);
+    } else {
+        pipe_variant_shape(index - pipe_first(), tx, ty);
     }
+}
+
+// kernel launches of one step with the current tile list
+int launches_per_step(const lbm_ctx* c) {
+    int n = c->has_tiny ? 1 : 0;
+    if (is_pipe(c->tile_index))
+        n += (c->n_fast > 0 ? 1 : 0) + (c->n_tiles > 0 ? 1 : 0);
+    else
+        n += 1;
+    return n;
 }
 
 // Tensor maps for a TMA variant's box shape (built once per context and
@@ -265,34 +287,73 @@ int build_tma(lbm_ctx* c, int tile_index) {
 // Work-list of one step launch: every tile of every lattice, lattices in
 // creation order, tiles row-major within a lattice.
 int build_tiles(lbm_ctx* c, int tile_index) {
+    if (tile_index < 0 || tile_index >= total_tiles()) return fail(LBM_EINVAL, "no tile shape %d", tile_index);
     if (tile_index >= kTileCount && c->precision == LBM_FP64)
-        return fail(LBM_EINVAL, "tile %d is an FP32 (TMA) variant; this context stores FP64", tile_index);
+        return fail(LBM_EINVAL, "tile %d is an FP32-only variant; this context stores FP64", tile_index);
+    const bool pipe = is_pipe(tile_index);
     int tx = 0, ty = 0;
     tile_shape(tile_index, &tx, &ty);
     std::vector<Tile> tiles;
+    std::vector<FastTile> fast;
     for (int l = 0; l < c->n; ++l) {
         const Geom& g = c->lats[l].geom;
         for (int y0 = 0; y0 < g.ny; y0 += ty)
-            for (int x0 = 0; x0 < g.nx; x0 += tx) tiles.push_back(Tile{l, x0, y0, 0});
+            for (int x0 = 0; x0 < g.nx; x0 += tx) {
+                // the pipelined kernel takes full tiles of wall-free lattices of at least 4 x 4
+                if (pipe && !g.has_mask && x0 + tx <= g.nx && y0 + ty <= g.ny && g.nx >= 4 && g.ny >= 4) {
+                    const int edge = x0 < 2 || x0 + tx > g.nx - 2 || y0 < 2 || y0 + ty > g.ny - 2;
+                    fast.push_back(FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, edge, {0, 0}});
+                } else {
+                    tiles.push_back(Tile{l, x0, y0, 0});
+                }
+            }
     }
-    if (tiles.size() > (size_t)0x7fffffff) return fail(LBM_EINVAL, "too many tiles");
+    if (tiles.size() > (size_t)0x7fffffff || fast.size() > (size_t)0x7fffffff)
+        return fail(LBM_EINVAL, "too many tiles");
     Tile* d = nullptr;
-    int rc = dev_alloc(c, &d, tiles.size() * sizeof(Tile));
-    if (rc) return rc;
-    cudaError_t e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
+    FastTile* df = nullptr;
+    int rc = 0;
+    if (!tiles.empty()) rc = dev_alloc(c, &d, tiles.size() * sizeof(Tile));
+    if (!rc && !fast.empty()) rc = dev_alloc(c, &df, fast.size() * sizeof(FastTile));
+    if (rc) {
+        if (d) {
+            cudaFree(d);
+            c->device_bytes -= tiles.size() * sizeof(Tile);
+        }
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (d) e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && df) e = cudaMemcpy(df, fast.data(), fast.size() * sizeof(FastTile), cudaMemcpyHostToDevice);
+    int per_sm = 0, sms = 0, dev = 0;
+    if (e == cudaSuccess && pipe) {
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        per_sm = pipe_blocks_per_sm(tile_index - pipe_first(), c->n <= kParamLattices);
+    }
+    if (e != cudaSuccess || (pipe && per_sm < 1)) {
         cudaFree(d);
-        return cuda_fail(e, "cudaMemcpy(tiles)");
+        cudaFree(df);
+        c->device_bytes -= tiles.size() * sizeof(Tile) + fast.size() * sizeof(FastTile);
+        return e != cudaSuccess ? cuda_fail(e, "tile list upload")
+                                : fail(LBM_ECUDA, "pipelined variant %d cannot be resident on this device", tile_index);
     }
     if (c->d_tiles) {
         cudaFree(c->d_tiles);
         c->device_bytes -= (size_t)c->n_tiles * sizeof(Tile);
     }
+    if (c->d_fast) {
+        cudaFree(c->d_fast);
+        c->device_bytes -= (size_t)c->n_fast * sizeof(FastTile);
+    }
     c->d_tiles = d;
     c->n_tiles = (int)tiles.size();
+    c->d_fast = df;
+    c->n_fast = (int)fast.size();
+    c->pipe_grid = pipe ? (int)std::min<long long>(c->n_fast, (long long)per_sm * sms) : 0;
     c->tile_index = tile_index;
     drop_graphs(c);
-    if (tile_index >= kTileCount) return build_tma(c, tile_index);
+    if (is_tma(tile_index)) return build_tma(c, tile_index);
     return LBM_OK;
 }
 
@@ -329,6 +390,16 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
                            (double*)c->f[1 - src], c->d_mask, c->d_status};
         e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
+    } else if (is_pipe(c->tile_index)) {
+        const int v = c->tile_index - pipe_first();
+        const PhysTable<float>* table = c->n <= kParamLattices ? c->h_table : nullptr;
+        PipeArgs pa{c->d_fast, c->n_fast, c->d_phys_f, (const float*)c->f[src], (float*)c->f[1 - src], c->d_status};
+        e = launch_step_pipe(v, c->pipe_grid, pa, table, c->stream);
+        if (e == cudaSuccess && c->n_tiles > 0) {
+            StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
+                              (float*)c->f[1 - src], c->d_mask, c->d_status};
+            e = launch_step_f32(pipe_plain_partner(v), c->n_tiles, a, c->h_table, c->stream);
+        }
     } else if (c->tile_index >= kTileCount) {
         const int v = c->tile_index - kTileCount;
         TmaArgs a{c->d_tiles, c->n_tiles, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status,
@@ -689,7 +760,7 @@ int lbm_step(lbm_ctx* c, int n) {
             int rc = ensure_graph(c, c->cur);
             if (rc) return rc;
             CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            c->launches += kGraphChunk * (c->has_tiny ? 2 : 1);
+            c->launches += kGraphChunk * launches_per_step(c);
             done += kGraphChunk;
             c->steps += kGraphChunk;  // kGraphChunk is even: c->cur unchanged
         }
@@ -697,7 +768,7 @@ int lbm_step(lbm_ctx* c, int n) {
     for (; done < n; ++done) {
         cudaError_t e = launch_one_step(c, c->cur);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        c->launches += c->has_tiny ? 2 : 1;
+        c->launches += launches_per_step(c);
         c->cur ^= 1;
         c->steps += 1;
     }
@@ -878,6 +949,14 @@ int lbm_tile_shape(int index, int* tx, int* ty) {
     return LBM_OK;
 }
 
+int lbm_tile_kind(int index, int* kind) {
+    if (index < 0 || index >= total_tiles())
+        return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, total_tiles());
+    if (!kind) return fail(LBM_EINVAL, "null argument");
+    *kind = is_pipe(index) ? LBM_TILE_PIPELINED : is_tma(index) ? LBM_TILE_TMA : LBM_TILE_PLAIN;
+    return LBM_OK;
+}
+
 int lbm_set_tile(lbm_ctx* c, int index) {
     if (!c) return fail(LBM_EINVAL, "null context");
     if (index < 0 || index >= total_tiles())
@@ -917,7 +996,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
         return cuda_fail(e, "autotune set-up");
     }
     for (int t = 0; t < total_tiles(); ++t) {
-        if (t >= kTileCount && (c->precision == LBM_FP64 || c->n > kTmaMaxLattices)) {
+        if ((t >= kTileCount && c->precision == LBM_FP64) || (is_tma(t) && c->n > kTmaMaxLattices)) {
             if (ms) ms[t] = -1.0;  // FP32-only variant, or too many lattices for it
             continue;
         }
@@ -925,12 +1004,12 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
         if (rc) break;
         // warm-up launch, then the timed steps
         e = launch_one_step(c, c->cur);
-        c->launches += c->has_tiny ? 2 : 1;
+        c->launches += launches_per_step(c);
         c->cur ^= 1;
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
         for (int k = 0; k < steps && e == cudaSuccess; ++k) {
             e = launch_one_step(c, c->cur);
-            c->launches += c->has_tiny ? 2 : 1;
+            c->launches += launches_per_step(c);
             c->cur ^= 1;
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
@@ -985,7 +1064,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->kernel_launches = c->launches;
     info->device_bytes = c->device_bytes;
     tile_shape(c->tile_index, &info->tile_x, &info->tile_y);
-    info->n_tiles = c->n_tiles;
+    info->n_tiles = c->n_tiles + c->n_fast;
     info->graph_chunk = kGraphChunk;
     return LBM_OK;
 }

@@ -53,6 +53,30 @@ cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps&
 bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const float* buf1,
                          const uint8_t* mask_base, CUtensorMap* fmaps2, CUtensorMap* mmap);
 
+// Persistent software-pipelined FP32 variants (lbm_step_pipe.cu); tile
+// indices kTileCount + tma_variant_count() + v. They take the full wall-free
+// tiles (FastTile list); the other tiles of the step go through the plain
+// kernel of the same node tile (pipe_plain_partner) in a second launch.
+struct FastTile {
+    long long f_off;       // plane 0 of the tile's lattice (element offset, both buffers)
+    int plane, pitch, nx, ny;
+    int lat, x0, y0, edge; // edge: within two cells of a lattice edge (writes ghost images)
+    int pad[2];
+};
+struct PipeArgs {
+    const FastTile* fast;
+    int n_fast;
+    const Phys<float>* phys;   // used when the parameters do not travel as a kernel argument
+    const float* fin;
+    float* fout;
+    unsigned* status;
+};
+int pipe_variant_count();
+void pipe_variant_shape(int v, int* tx, int* ty);
+int pipe_plain_partner(int v);
+int pipe_blocks_per_sm(int v, bool table);
+cudaError_t launch_step_pipe(int v, int grid, const PipeArgs& a, const PhysTable<float>* table, cudaStream_t s);
+
 // table: the batch's parameters for the constant-bank path (batches of at
 // most kParamLattices lattices), or null to read them from global memory.
 cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a,

@@ -207,6 +207,58 @@ __device__ __forceinline__ void pull_pair(const float* __restrict__ fin, int pla
     f[8] = ld2(8 * plane + c + pitch - 1);
 }
 
+// Force (Eq. 7), collision (Eq. 3) and store of the node pair in tile-local
+// column lx, rows ly and ly + 1 (psi tile s_psi with a one-cell frame, row
+// stride SW), lattice column x, rows y and y + 1, stored index cs of the
+// first node; the ghost images too when the tile is near an edge.
+template <int SW>
+__device__ __forceinline__ void f32_pair_finish(F2 (&f)[9], F2 rho, F2 drho, F2 psi, const float* s_psi, int lx,
+                                                int ly, const Phys<float>& P, float* __restrict__ fo, int cs,
+                                                bool edge, const Geom& g, int x, int y) {
+    const int plane = (int)g.plane, pitch = g.pitch;
+    const int c = (ly + 1) * SW + lx + 1;
+    auto nb2 = [&](int o) { return F2{make_float2(s_psi[c + o], s_psi[c + SW + o])}; };
+    F2 gx, gy;
+    vforce_sum(nb2(1), nb2(SW), nb2(-1), nb2(-SW), nb2(SW + 1), nb2(SW - 1), nb2(-SW - 1), nb2(-SW + 1), gx, gy);
+    const F2 mGpsi = splat<F2>(-P.G) * psi;
+    const F2 Fx = mGpsi * gx, Fy = mGpsi * gy;
+    const F2 g2G2 = splat<F2>(__fmul_rn(P.G, P.G)) * vfma(gx, gx, gy * gy);
+    vcollide(f, rho, drho, Fx, Fy, g2G2, P);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        fo[a * plane + cs] = f[a].v.x;
+        fo[a * plane + cs + pitch] = f[a].v.y;
+    }
+    if (edge) {
+        float v0[9], v1[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            v0[a] = f[a].v.x;
+            v1[a] = f[a].v.y;
+        }
+        store_images<float>(fo, g, cs, x, y, v0);
+        store_images<float>(fo, g, cs + pitch, x, y + 1, v1);
+    }
+}
+
+// Position (cx, cy) in the psi tile (SW x SH, one-cell frame around a
+// TX x TY tile) of halo ring cell h: top row, bottom row, then the left and
+// right columns alternately.
+template <int SW, int SH>
+__device__ __forceinline__ void halo_ring_cell(int h, int& cx, int& cy) {
+    if (h < SW) {
+        cx = h;
+        cy = 0;
+    } else if (h < 2 * SW) {
+        cx = h - SW;
+        cy = SH - 1;
+    } else {
+        const int q = h - 2 * SW;
+        cy = 1 + (q >> 1);
+        cx = (q & 1) ? SW - 1 : 0;
+    }
+}
+
 template <int TX, int TYT, int RY>
 __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Tile& tile, const Geom& g,
                                               const Phys<float>& P, float* s_psi) {
@@ -240,17 +292,7 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
         hc[k] = -1;
         if (h < NH) {
             int cx, cy;
-            if (h < SW) {
-                cx = h;
-                cy = 0;
-            } else if (h < 2 * SW) {
-                cx = h - SW;
-                cy = SH - 1;
-            } else {
-                const int q = h - 2 * SW;
-                cy = 1 + (q >> 1);
-                cx = (q & 1) ? SW - 1 : 0;
-            }
+            halo_ring_cell<SW, SH>(h, cx, cy);
             hc[k] = cy * SW + cx;
             float fh[9];
             pull_node<float>(fin, nullptr, plane, pitch, node_index(g, tile.x0 - 1 + cx, tile.y0 - 1 + cy), fh);
@@ -276,37 +318,10 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
 
     float* __restrict__ fo = A.fout + g.f_off;
     const bool edge = tile.x0 < 2 || tile.x0 + TX > g.nx - 2 || tile.y0 < 2 || tile.y0 + TY > g.ny - 2;
-    const F2 mG = splat<F2>(-P.G);
-    const F2 G2 = splat<F2>(__fmul_rn(P.G, P.G));
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        // force, Eq. 7, from the psi tile (row stride SW)
-        const int c = (ly0 + 2 * p + 1) * SW + lx + 1;
-        auto nb2 = [&](int o) { return F2{make_float2(s_psi[c + o], s_psi[c + SW + o])}; };
-        F2 gx, gy;
-        vforce_sum(nb2(1), nb2(SW), nb2(-1), nb2(-SW), nb2(SW + 1), nb2(SW - 1), nb2(-SW - 1), nb2(-SW + 1), gx, gy);
-        const F2 mGpsi = mG * psi[p];
-        const F2 Fx = mGpsi * gx, Fy = mGpsi * gy;
-        const F2 g2G2 = G2 * vfma(gx, gx, gy * gy);
-        // collision, Eq. 3, and the store of f*
-        vcollide(f[p], rho[p], drho[p], Fx, Fy, g2G2, P);
-        const int cs = c0 + 2 * p * pitch;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            fo[a * plane + cs] = f[p][a].v.x;
-            fo[a * plane + cs + pitch] = f[p][a].v.y;
-        }
-        if (edge) {
-            float v0[9], v1[9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                v0[a] = f[p][a].v.x;
-                v1[a] = f[p][a].v.y;
-            }
-            store_images<float>(fo, g, cs, x, y0 + 2 * p, v0);
-            store_images<float>(fo, g, cs + pitch, x, y0 + 2 * p + 1, v1);
-        }
-    }
+    for (int p = 0; p < NP; ++p)
+        f32_pair_finish<SW>(f[p], rho[p], drho[p], psi[p], s_psi, lx, ly0 + 2 * p, P, fo, c0 + 2 * p * pitch, edge,
+                            g, x, y0 + 2 * p);
 }
 
 // One tile by the general path (any tile: partial, walled, tiny lattices).

@@ -38,7 +38,7 @@ EXPORTED = [
     "lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_init_fields", "lbm_init_fields_all",
     "lbm_step", "lbm_read_moments", "lbm_read_moments_all", "lbm_total_mass", "lbm_status",
     "lbm_clear_status", "lbm_sync", "lbm_state_size", "lbm_save_state", "lbm_load_state",
-    "lbm_tile_count", "lbm_tile_shape", "lbm_set_tile", "lbm_autotune", "lbm_info",
+    "lbm_tile_count", "lbm_tile_shape", "lbm_tile_kind", "lbm_set_tile", "lbm_autotune", "lbm_info",
     "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc",
 ]
 
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_load_state.argtypes = [_ctx, _vp, ctypes.c_size_t]
     lib.lbm_tile_count.argtypes = []
     lib.lbm_tile_shape.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.lbm_tile_kind.argtypes = [I, ctypes.POINTER(I)]
     lib.lbm_set_tile.argtypes = [_ctx, I]
     lib.lbm_autotune.argtypes = [_ctx, I, ctypes.POINTER(I), _dp]
     lib.lbm_info.argtypes = [_ctx, ctypes.POINTER(lbm_info_t)]
@@ -230,6 +231,15 @@ def lbm_tile_shape(i):
     tx, ty = ctypes.c_int(), ctypes.c_int()
     _check(load().lbm_tile_shape(i, ctypes.byref(tx), ctypes.byref(ty)))
     return tx.value, ty.value
+
+
+LBM_TILE_PLAIN, LBM_TILE_TMA, LBM_TILE_PIPELINED = 0, 1, 2
+
+
+def lbm_tile_kind(i):
+    k = ctypes.c_int()
+    _check(load().lbm_tile_kind(i, ctypes.byref(k)))
+    return k.value
 
 
 def lbm_set_tile(ctx, i):

@@ -38,6 +38,10 @@ def test_tile_table():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_tile_shape(n)
     assert e.value.code == lbm.LBM_EINVAL
+    kinds = [lbm.lbm_tile_kind(i) for i in range(n)]
+    assert kinds[0] == lbm.LBM_TILE_PLAIN and set(kinds) <= {0, 1, 2} and 2 in kinds
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_tile_kind(-1)
 
 
 def _desc(**kw):

@@ -92,6 +92,23 @@ def test_every_tile_is_bitwise_identical(precision):
                 assert np.array_equal(x, y), f"tile {lbm.lbm_tile_shape(t)}"
 
 
+def test_pipelined_variants_walk_many_tiles_bitwise():
+    """The persistent pipelined variants take more full tiles than they have
+    CTAs (each CTA walks several, with the next tile's loads in flight), next
+    to partial and walled tiles that go through the plain kernel in the same
+    step; every node matches the one-tile-per-CTA kernel bit for bit."""
+    specs = [small_spec(1024, 192, seed=11), small_spec(70, 45, walls=True), small_spec(130, 9),
+             small_spec(256, 64, seed=12, shape="bubble")]
+    ref = run_gpu(specs, "fp32_dev", 6, tile=0)
+    pipes = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_PIPELINED]
+    assert pipes
+    for t in pipes:
+        got = run_gpu(specs, "fp32_dev", 6, tile=t)
+        for a, b in zip(ref, got):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), f"tile {t} {lbm.lbm_tile_shape(t)}"
+
+
 def test_batch_equals_individual_runs():
     specs = [small_spec(40, 30, seed=1), small_spec(97, 31, walls=True, seed=2),
              small_spec(16, 80, seed=3, shape="bubble"), small_spec(5, 3, seed=4)]
@@ -297,7 +314,7 @@ def test_tma_wait_timeout_reports_etimeout_and_context_recovers(monkeypatch):
     reports LBM_ETIMEOUT. A context with the normal settings then steps
     correctly."""
     specs = [small_spec(64, 40, seed=21)]
-    tma = [t for t in range(lbm.lbm_tile_count()) if t >= 9]
+    tma = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_TMA]
     if not tma:
         pytest.skip("no TMA variants")
     monkeypatch.setenv("LBM_TMA_WAIT_CYCLES", "2000000")
