@@ -36,7 +36,7 @@ ALG_BYTES_FP64 = 144
 WORKLOAD = "coexistence_batch"
 PROFILE = os.path.join(ROOT, "profiles", "step_fp32_coexistence_batch.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1605_01800_gb300", "csrc", f)
-                  for f in ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu")]
+                  for f in ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu", "lbm_step_pipe.cu")]
 
 
 def parse_args():

@@ -144,7 +144,9 @@ int lbm_step(lbm_ctx* ctx, int n);
 
 /* Macroscopic fields of lattice `lat` at the current time: rho = sum_a f_a,
  * v of Eq. 6 (with the force of Eq. 7), p of Eq. 10. Host outputs of nx*ny
- * doubles; any may be NULL. Solid nodes read as 0. Synchronises the stream. */
+ * doubles; any may be NULL (with ux, uy and p all NULL only the density is
+ * computed, by a lighter kernel, with the same values). Solid nodes read as 0.
+ * Synchronises the stream. */
 int lbm_read_moments(lbm_ctx* ctx, int lat, double* rho, double* ux, double* uy, double* p);
 
 /* lbm_read_moments for every lattice, outputs concatenated in creation order. */

@@ -551,12 +551,17 @@ int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, doub
     double* d[4] = {c->d_io, c->d_io + N, c->d_io + 2 * N, c->d_io + 3 * N};
     const LaunchSet ls = launch_set(c, lat0, n_lat);
     cudaError_t e;
-    if (c->precision == LBM_FP64)
-        e = launch_moments_f64(ls, (const double*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream);
-    else
-        e = launch_moments_f32(ls, (const float*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream);
+    if (!ux && !uy && !p) {  // density only: one light kernel
+        e = c->precision == LBM_FP64 ? launch_density_f64(ls, (const double*)c->f[c->cur], d[0], c->stream)
+                                     : launch_density_f32(ls, (const float*)c->f[c->cur], d[0], c->stream);
+        c->launches += 1;
+    } else {
+        e = c->precision == LBM_FP64
+                ? launch_moments_f64(ls, (const double*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream)
+                : launch_moments_f32(ls, (const float*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream);
+        c->launches += 2;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
-    c->launches += 2;
     const long long base = c->lats[lat0].geom.node_off;
     const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
     double* h[4] = {rho, ux, uy, p};

@@ -136,6 +136,29 @@ __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<do
     }
 }
 
+// Read-out of the density alone (when no other moment is asked for): rho of
+// every node from its pulled distribution, summed in FP64 in the order of
+// moments_psi_kernel (so both give the same value), 0 at solid nodes.
+template <typename T>
+__global__ void density_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys, int lat0,
+                               const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
+                               double* __restrict__ rho_out) {
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    const double rho_ref = phys[lat].rho_ref;
+    const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
+    const T* f = f_base + g.f_off;
+    const int n = g.nx * g.ny;  // < 2^31: 9 stored planes hold fewer than 2^31 elements
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / g.nx, x = i - y * g.nx;
+        double fc[9];
+        double rho = 0.0;
+        if (pulled_fp64<T>(g, f, mask, rho_ref, x, y, fc))
+            for (int a = 0; a < 9; ++a) rho += fc[a];
+        rho_out[g.node_off + i] = rho;
+    }
+}
+
 // Read-out, pass 2: force (Eq. 7, a solid neighbour takes the node's psi),
 // velocity (Eq. 6) and pressure (Eq. 10) of every node; ux/uy hold the
 // momentum on entry and the velocity on exit.
@@ -257,6 +280,13 @@ cudaError_t moments_impl(const LaunchSet& L, const T* f, double* psi, double* rh
 }
 
 template <typename T>
+cudaError_t density_impl(const LaunchSet& L, const T* f, double* rho, cudaStream_t s) {
+    density_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(L.geoms, L.phys, L.lat0, f, L.mask,
+                                                                               rho);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T* f,
                       const uint8_t* mask, double* partials, double* out, cudaStream_t s) {
     mass_partial_kernel<T><<<kMassBlocks, kMassThreads, 0, s>>>(g, f + g.f_off, mask, partials);
@@ -289,6 +319,13 @@ cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double*
                             const double* uy, double* f, unsigned* bad, cudaStream_t s) {
     return init_impl<double>(L, rho, ux, uy, f, bad, s);
 }
+cudaError_t launch_density_f32(const LaunchSet& L, const float* f, double* rho, cudaStream_t s) {
+    return density_impl<float>(L, f, rho, s);
+}
+cudaError_t launch_density_f64(const LaunchSet& L, const double* f, double* rho, cudaStream_t s) {
+    return density_impl<double>(L, f, rho, s);
+}
+
 cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s) {
     return moments_impl<float>(L, f, psi, rho, ux, uy, p, s);

@@ -109,6 +109,10 @@ cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* psi, 
 cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s);
 
+// rho alone (the first output of launch_moments_*, same values).
+cudaError_t launch_density_f32(const LaunchSet& L, const float* f, double* rho, cudaStream_t s);
+cudaError_t launch_density_f64(const LaunchSet& L, const double* f, double* rho, cudaStream_t s);
+
 // Rewrite the ghost frames of lattices [lat0, lat0 + n_lat) from their nodes.
 cudaError_t launch_ghost_refresh_f32(const LaunchSet& L, float* f, cudaStream_t s);
 cudaError_t launch_ghost_refresh_f64(const LaunchSet& L, double* f, cudaStream_t s);

@@ -333,3 +333,23 @@ def test_tma_wait_timeout_reports_etimeout_and_context_recovers(monkeypatch):
     (ref,) = run_gpu(specs, "fp32_dev", 3, tile=0)
     for x, y in zip(ok, ref):
         assert np.array_equal(x, y)
+
+
+def test_density_only_readout_equals_full_readout():
+    """With ux, uy and p all NULL the read-out takes the density-only kernel;
+    its rho equals the full read-out's bit for bit, walls and batches included."""
+    specs = [small_spec(48, 40, walls=True, seed=31), small_spec(33, 17, seed=32), small_spec(5, 3, seed=33)]
+    for precision in ("fp32_dev", "fp64"):
+        b = lbm.Batch(specs, precision)
+        b.init()
+        b.step(5)
+        n = sum(s.nodes for s in specs)
+        rho_only = np.empty(n)
+        lbm.lbm_read_moments_all(b.ctx, rho_only)
+        full = [np.empty(n) for _ in range(4)]
+        lbm.lbm_read_moments_all(b.ctx, *full)
+        assert np.array_equal(rho_only, full[0])
+        one = np.empty(specs[0].nodes)
+        lbm.lbm_read_moments(b.ctx, 0, one)
+        assert np.array_equal(one, full[0][:specs[0].nodes])
+        b.close()
