@@ -55,7 +55,7 @@ def measure_bubbles(batch: "lbm.Batch") -> List[dict]:
 
 
 def laplace_fit(radii: Sequence[float], t_over_tc: float, steps: int, a: float = 1.0, tau_nu: float = 0.6,
-                eps: float = 1.86, n: int = 201, stream=None) -> dict:
+                eps: float = 1.86, n: int = 201, stream=None, precision: str = "fp32_dev") -> dict:
     """Run static bubbles for `steps` steps and fit the Laplace law.
 
     `sigma` is the least-squares slope of Eq. 17 as written, |dp| = sigma / r
@@ -63,7 +63,7 @@ def laplace_fit(radii: Sequence[float], t_over_tc: float, steps: int, a: float =
     fit |dp| = sigma / r + c, whose small intercept and r2 near 1 show that
     the bubbles obey the 1/r law."""
     specs = bubble_batch(radii, t_over_tc, a=a, n=n, tau_nu=tau_nu, eps=eps)
-    b = lbm.Batch(specs, "fp32_dev", stream=stream)
+    b = lbm.Batch(specs, precision, stream=stream)
     b.init()
     b.step(steps)
     rows = measure_bubbles(b)
@@ -224,14 +224,17 @@ def _vapour_components(vap: np.ndarray) -> int:
     return k
 
 
-def wall_collapse_run(steps: int, every: int = 500, stream=None, **kw) -> dict:
-    """Shape history of the collapsing bubble: vapour area, lateral and
-    vertical extent, number of vapour regions and the largest wall-normal
-    speed, every `every` steps."""
-    spec = wall_collapse_spec(**kw)
+def wall_collapse_run(steps: int, every: int = 500, stream=None, precision: str = "fp32_dev", spec=None,
+                      **kw) -> dict:
+    """Shape history of the collapsing bubble: vapour area, its equivalent
+    radius sqrt(area / pi), lateral and vertical extent, number of vapour
+    regions and the largest speeds, every `every` steps. `spec` (a lattice
+    with walls and meta rho_l, rho_g) replaces the Sec. 4.1 domain."""
+    if spec is None:
+        spec = wall_collapse_spec(**kw)
     rl, rg = spec.meta["rho_l"], spec.meta["rho_g"]
     thr = 0.5 * (rl + rg)
-    b = lbm.Batch([spec], "fp32_dev", stream=stream)
+    b = lbm.Batch([spec], precision, stream=stream)
     b.init()
     rows = []
     done = 0
@@ -239,7 +242,9 @@ def wall_collapse_run(steps: int, every: int = 500, stream=None, **kw) -> dict:
         rho, ux, uy, _ = b.moments(0, allow_flags=True)
         vap = (rho < thr) & (spec.solid == 0)
         ys, xs = np.nonzero(vap)
-        rows.append({"t": done, "area": int(vap.sum()),
+        wall = np.abs(uy[1:21, :])   # the 20 fluid rows above the lower wall
+        rows.append({"t": done, "area": int(vap.sum()), "r": float(np.sqrt(vap.sum() / np.pi)),
+                     "uy_wall": float(wall.max()) if np.all(np.isfinite(wall)) else float("nan"),
                      "width": int(xs.max() - xs.min() + 1) if xs.size else 0,
                      "height": int(ys.max() - ys.min() + 1) if ys.size else 0,
                      "regions": _vapour_components(vap) if xs.size else 0,
