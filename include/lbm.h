@@ -62,16 +62,38 @@ extern "C" {
 
 typedef struct lbm_ctx lbm_ctx;
 
-/* Carnahan-Starling EOS of Eq. 15, p = rho R T (1 + h + h^2 - h^3)/(1 - h)^3
- * - a rho^2 with h = b rho / 4, and the interaction strength G of Eq. 7 and
- * Eq. 13 (G < 0; the paper uses G = -1). */
+/* The pseudopotential psi of a lattice and the interaction strength G of
+ * Eq. 7. `kind` selects psi:
+ *   LBM_EOS_CS   Eq. 13 with the Carnahan-Starling EOS of Eq. 15 (the paper's):
+ *                p = rho R T (1 + h + h^2 - h^3)/(1 - h)^3 - a rho^2, h = b rho / 4;
+ *   LBM_EOS_VDW  Eq. 13 with van der Waals, p = rho R T/(1 - b rho) - a rho^2;
+ *   LBM_EOS_PR   Eq. 13 with Peng-Robinson, p = rho R T/(1 - b rho)
+ *                - a alpha(T) rho^2/(1 + 2 b rho - b^2 rho^2), alpha =
+ *                (1 + k (1 - sqrt(T/Tc)))^2, k = 0.37464 + 1.54226 omega
+ *                - 0.26992 omega^2, Tc = 0.0778 a / (0.45724 b R);
+ *   LBM_PSI_EXP  Eq. 12 (the first strategy): psi = exp(-1/rho) for e = 0,
+ *                (rho/(e + rho))^(1/e) otherwise, with e = -G eps: the
+ *                mechanical-stability exponent that Li's term with the
+ *                lattice's eps (Eq. 14) produces (e = eps at G = -1), so the
+ *                model meets Eq. 11 by construction; a, b, R, T, omega
+ *                unused; p of Eq. 10 is then the model's EOS (G < 0 with
+ *                |G| large enough for two phases, e.g. -3).
+ * For the Eq. 13 kinds G < 0 (the paper uses G = -1), b > 0, R T >= 0. The
+ * fastest step paths take LBM_EOS_CS lattices; the others run the general
+ * path. A zero-initialised `kind` and `omega` select the paper's EOS. */
+#define LBM_EOS_CS 0
+#define LBM_EOS_VDW 1
+#define LBM_EOS_PR 2
+#define LBM_PSI_EXP 3
 typedef struct {
     double a, b, R, T, G;
+    int kind;
+    double omega;   /* Peng-Robinson acentric factor */
 } lbm_eos_params;
 
 /* One lattice of a batch.
  *   nx, ny     lattice size, each >= 1; 9 * ny * round_up(nx, 32) < 2^31.
- *   eos        Eq. 15 and G.
+ *   eos        psi (Eq. 13 with an EOS, or Eq. 12) and G.
  *   s          diagonal of Lambda (Eq. 2) in the moment order
  *              (rho, e, zeta, j_x, q_x, j_y, q_y, p_xx, p_xy); each in [0, 2).
  *   eps        epsilon of Li's term, Eq. 14.

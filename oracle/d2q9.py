@@ -25,7 +25,11 @@ class OracleParams(ctypes.Structure):
                 ("G", ctypes.c_double),
                 ("s", ctypes.c_double * Q),
                 ("eps", ctypes.c_double),
-                ("solid", ctypes.c_void_p)]
+                ("solid", ctypes.c_void_p),
+                ("eos", ctypes.c_int),
+                ("omega", ctypes.c_double)]
+
+EOS_KINDS = {"cs": 0, "vdw": 1, "pr": 2, "psi_exp": 3}
 
 
 _lib = None
@@ -70,11 +74,14 @@ class Lattice:
 
     ``s`` is the diagonal of Lambda (Eq. 2) in the order
     (rho, e, zeta, j_x, q_x, j_y, q_y, p_xx, p_xy); ``eps`` is the epsilon of
-    Eq. 14; ``solid`` an optional (ny, nx) uint8 mask (1 = solid node).
+    Eq. 14; ``solid`` an optional (ny, nx) uint8 mask (1 = solid node);
+    ``eos`` the pseudopotential: "cs" (Eq. 13 with Eq. 15), "vdw" or "pr"
+    (Eq. 13 with van der Waals or Peng-Robinson), "psi_exp" (Eq. 12 with
+    the same eps); ``omega`` the Peng-Robinson acentric factor.
     """
 
     def __init__(self, nx, ny, a=1.0, b=4.0, R=1.0, T=0.0, G=-1.0, s=None, eps=0.0,
-                 solid=None):
+                 solid=None, eos="cs", omega=0.0):
         self.lib = _load()
         if s is None:
             s = [1.0] * Q
@@ -83,7 +90,8 @@ class Lattice:
         if solid is not None:
             self.solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(ny, nx)
         self.p = OracleParams(self.nx, self.ny, a, b, R, T, G, (ctypes.c_double * Q)(*s),
-                              eps, self.solid.ctypes.data if self.solid is not None else None)
+                              eps, self.solid.ctypes.data if self.solid is not None else None,
+                              EOS_KINDS[eos], omega)
         n = self.nx * self.ny
         self.f = np.zeros((Q, self.ny, self.nx))
         self._work = np.zeros((Q + 2) * n)

@@ -64,6 +64,9 @@ typedef struct {
     double s[Q];          /* diagonal of Lambda, Eq. 2, order (rho,e,zeta,j,q,j,q,nu,nu) */
     double eps;           /* epsilon of Eq. 14 */
     const unsigned char* solid; /* nx*ny, 1 = solid node; NULL = none */
+    int eos;              /* psi: 0 Eq. 13 with CS (Eq. 15), 1 Eq. 13 with van der Waals,
+                             2 Eq. 13 with Peng-Robinson, 3 Eq. 12 */
+    double omega;         /* Peng-Robinson acentric factor */
 } oracle_params;
 
 /* ---- moment matrix, Sec. 2.1 ------------------------------------------ */
@@ -117,17 +120,65 @@ void oracle_moment_matrix(double* m_out, double* minv_out) {
 
 /* ---- thermodynamics ---------------------------------------------------- */
 
-/* Carnahan-Starling EOS, Eq. 15. */
-double oracle_p_eos(const oracle_params* P, double rho) {
-    double eta = P->b * rho / 4.0;
-    double num = 1.0 + eta + eta * eta - eta * eta * eta;
-    double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);
-    return rho * P->R * P->T * num / den - P->a * rho * rho;
+/* Peng-Robinson temperature factor alpha(T) = (1 + k (1 - sqrt(T/Tc)))^2,
+ * k = 0.37464 + 1.54226 omega - 0.26992 omega^2; Tc follows from the PR
+ * constants a = 0.45724 R^2 Tc^2 / pc and b = 0.0778 R Tc / pc. */
+static double pr_alpha(const oracle_params* P) {
+    double Tc = (0.0778 / 0.45724) * P->a / (P->b * P->R);
+    double k = 0.37464 + 1.54226 * P->omega - 0.26992 * P->omega * P->omega;
+    double s = 1.0 + k * (1.0 - sqrt(P->T / Tc));
+    return s * s;
 }
 
-/* Square-root pseudopotential, Eq. 13 (c = 1). Sets *flag on clamping or a
- * non-finite value. */
+/* psi of Eq. 12 (the first strategy): exp(-1/rho) for e = 0, else
+ * (rho / (e + rho))^(1/e), where e = -G eps is the exponent of the
+ * mechanical stability condition (Eq. 9) that Li's term with eps yields
+ * (Li et al. 2013: e = -16 G sigma with 0.75 eps = 12 sigma; e = eps at the
+ * paper's G = -1). */
+static double psi_eq12(const oracle_params* P, double rho) {
+    double e = -P->G * P->eps;
+    if (e == 0.0) return exp(-1.0 / rho);
+    return pow(rho / (e + rho), 1.0 / e);
+}
+
+/* Non-ideal LB pressure, Eq. 10 (c = 1). */
+double oracle_pressure(const oracle_params* P, double rho, double psi) {
+    return rho * CS2 + 0.5 * P->G * psi * psi;
+}
+
+/* The EOS: Carnahan-Starling (Eq. 15, the paper's), van der Waals or
+ * Peng-Robinson for Eq. 13; for the Eq. 12 psi the EOS the model produces,
+ * Eq. 10. */
+double oracle_p_eos(const oracle_params* P, double rho) {
+    double RT = P->R * P->T;
+    switch (P->eos) {
+    case 1: /* van der Waals */
+        return rho * RT / (1.0 - P->b * rho) - P->a * rho * rho;
+    case 2: /* Peng-Robinson */
+        return rho * RT / (1.0 - P->b * rho) -
+               P->a * pr_alpha(P) * rho * rho / (1.0 + 2.0 * P->b * rho - P->b * P->b * rho * rho);
+    case 3: /* Eq. 12 psi in Eq. 10 */
+        return oracle_pressure(P, rho, psi_eq12(P, rho));
+    default: { /* Carnahan-Starling, Eq. 15 */
+        double eta = P->b * rho / 4.0;
+        double num = 1.0 + eta + eta * eta - eta * eta * eta;
+        double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);
+        return rho * RT * num / den - P->a * rho * rho;
+    }
+    }
+}
+
+/* Pseudopotential (c = 1): Eq. 12 for eos 3, else the square root of Eq. 13.
+ * Sets *flag on clamping or a non-finite value. */
 double oracle_psi(const oracle_params* P, double rho, unsigned* flag) {
+    if (P->eos == 3) {
+        double v = rho > 0.0 ? psi_eq12(P, rho) : NAN;
+        if (!isfinite(v)) {
+            if (flag) *flag |= OR_FLAG_NONFINITE;
+            return 0.0;
+        }
+        return v;
+    }
     double arg = 2.0 * (oracle_p_eos(P, rho) - rho * CS2) / P->G;
     if (!isfinite(arg)) {
         if (flag) *flag |= OR_FLAG_NONFINITE;
@@ -138,11 +189,6 @@ double oracle_psi(const oracle_params* P, double rho, unsigned* flag) {
         return 0.0;
     }
     return sqrt(arg);
-}
-
-/* Non-ideal LB pressure, Eq. 10 (c = 1). */
-double oracle_pressure(const oracle_params* P, double rho, double psi) {
-    return rho * CS2 + 0.5 * P->G * psi * psi;
 }
 
 /* ---- helpers ----------------------------------------------------------- */

@@ -121,13 +121,17 @@ def psi_sq(rho, T, a=1.0, b=4.0, R=1.0, G=-1.0):
 def lb_coexistence(T, eps, a=1.0, b=4.0, R=1.0, G=-1.0):
     """Coexistence (rho_g, rho_l, p0) of the pseudopotential model from the
     mechanical stability condition Eq. 9, with psi of Eq. 13 and
-    p_EOS-PL = p_EOS. The weight psi'/psi^(1+eps) is evaluated with
-    psi' = (dp/drho - c_s^2) / (G psi), which follows from Eq. 13."""
+    p_EOS-PL = p_EOS. The weight psi'/psi^(1+e) is evaluated with
+    psi' = (dp/drho - c_s^2) / (G psi), which follows from Eq. 13; the
+    exponent e = -G eps is the one Li's term of Eq. 14 with coefficient eps
+    produces (eps itself at the paper's G = -1)."""
+    e = -G * eps
+
     def weight(r):
         s2 = psi_sq(r, T, a, b, R, G)
         psi = math.sqrt(s2)
         dpsi = (dp_drho(r, T, a, b, R) - CS2) / (G * psi)
-        return dpsi / psi ** (1.0 + eps)
+        return dpsi / psi ** (1.0 + e)
     return _coexistence(T, weight, a, b, R)
 
 

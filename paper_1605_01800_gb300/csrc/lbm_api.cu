@@ -133,9 +133,17 @@ int validate_desc(const lbm_lattice_desc& d, int i) {
     if (!(std::isfinite(e.a) && std::isfinite(e.b) && std::isfinite(e.R) && std::isfinite(e.T) &&
           std::isfinite(e.G)))
         return fail(LBM_EINVAL, "lattice %d: EOS parameters must be finite", i);
-    if (!(e.b > 0.0)) return fail(LBM_EINVAL, "lattice %d: b must be > 0 (Eq. 15)", i);
-    if (!(e.G < 0.0)) return fail(LBM_EINVAL, "lattice %d: G must be < 0 for psi of Eq. 13", i);
-    if (!(e.R * e.T >= 0.0)) return fail(LBM_EINVAL, "lattice %d: R*T must be >= 0", i);
+    if (e.kind < LBM_EOS_CS || e.kind > LBM_PSI_EXP) return fail(LBM_EINVAL, "lattice %d: unknown psi kind %d", i, e.kind);
+    if (e.kind == LBM_PSI_EXP) {
+        if (!(e.G != 0.0 && std::isfinite(e.G))) return fail(LBM_EINVAL, "lattice %d: G must be finite and nonzero", i);
+        if (!(d.eps >= 0.0)) return fail(LBM_EINVAL, "lattice %d: eps must be >= 0 for psi of Eq. 12", i);
+    } else {
+        if (!(e.b > 0.0)) return fail(LBM_EINVAL, "lattice %d: b must be > 0", i);
+        if (!(e.G < 0.0)) return fail(LBM_EINVAL, "lattice %d: G must be < 0 for psi of Eq. 13", i);
+        if (!(e.R * e.T >= 0.0)) return fail(LBM_EINVAL, "lattice %d: R*T must be >= 0", i);
+        if (e.kind == LBM_EOS_PR && !(e.a > 0.0 && e.R > 0.0 && e.T >= 0.0 && std::isfinite(e.omega)))
+            return fail(LBM_EINVAL, "lattice %d: Peng-Robinson needs a > 0, R > 0, T >= 0, finite omega", i);
+    }
     for (int k = 0; k < 9; ++k)
         if (!(d.s[k] >= 0.0 && d.s[k] < 2.0))
             return fail(LBM_EINVAL, "lattice %d: relaxation rate s[%d]=%g outside [0, 2)", i, k, d.s[k]);
@@ -159,6 +167,21 @@ void fill_phys(const HostLattice& L, Phys<double>& P) {
     }
     P.li_e = d.s[1] * 0.75 * d.eps;
     P.li_z = d.s[2] * 0.75 * d.eps;
+    P.eos = d.eos.kind;
+    P.b1 = d.eos.b;
+    // Eq. 12's exponent is the mechanical-stability eps that Li's forcing
+    // with this lattice's eps produces, -G eps (Li et al. 2013; = eps at the
+    // paper's G = -1), so that psi'/psi^(1+e) = 1/rho^2 holds for the model
+    const double e12 = -d.eos.G * d.eps;
+    P.eps12 = e12;
+    P.inv_eps12 = e12 != 0.0 ? 1.0 / e12 : 0.0;
+    if (d.eos.kind == LBM_EOS_PR) {
+        // a alpha(T): Tc from a = 0.45724 R^2 Tc^2 / pc and b = 0.0778 R Tc / pc
+        const double Tc = 0.0778 * d.eos.a / (0.45724 * d.eos.b * d.eos.R);
+        const double k = 0.37464 + 1.54226 * d.eos.omega - 0.26992 * d.eos.omega * d.eos.omega;
+        const double s = 1.0 + k * (1.0 - std::sqrt(d.eos.T / Tc));
+        P.a = d.eos.a * s * s;
+    }
 }
 
 void to_float(const Phys<double>& D, Phys<float>& F) {
@@ -175,6 +198,10 @@ void to_float(const Phys<double>& D, Phys<float>& F) {
     }
     F.li_e = (float)D.li_e;
     F.li_z = (float)D.li_z;
+    F.b1 = (float)D.b1;
+    F.eps12 = (float)D.eps12;
+    F.inv_eps12 = (float)D.inv_eps12;
+    F.eos = D.eos;
 }
 
 template <typename P>
@@ -299,8 +326,9 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         const Geom& g = c->lats[l].geom;
         for (int y0 = 0; y0 < g.ny; y0 += ty)
             for (int x0 = 0; x0 < g.nx; x0 += tx) {
-                // the pipelined kernel takes full tiles of wall-free lattices of at least 4 x 4
-                if (pipe && !g.has_mask && x0 + tx <= g.nx && y0 + ty <= g.ny && g.nx >= 4 && g.ny >= 4) {
+                // the pipelined kernel takes full tiles of wall-free Carnahan-Starling lattices of at least 4 x 4
+                if (pipe && !g.has_mask && x0 + tx <= g.nx && y0 + ty <= g.ny && g.nx >= 4 && g.ny >= 4 &&
+                    c->lats[l].desc.eos.kind == LBM_EOS_CS) {
                     const int edge = x0 < 2 || x0 + tx > g.nx - 2 || y0 < 2 || y0 + ty > g.ny - 2;
                     fast.push_back(FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, edge, {0, 0}});
                 } else {

@@ -55,7 +55,15 @@ struct Phys {
     T s[9];               // diagonal of Lambda, Eq. 2
     T h[9];               // 1 - s/2, the factor of S in Eq. 3
     T li_e, li_z;         // s_e * 0.75 eps and s_zeta * 0.75 eps (Li's term after (1 - s/2))
+    T b1;                 // b of the van der Waals and Peng-Robinson EOS
+    T eps12, inv_eps12;   // eps of Eq. 12 and 1 / eps (0 when eps = 0)
+    int eos;              // EOS_CS, EOS_VDW, EOS_PR (a holds a alpha(T)), PSI_EXP (Eq. 12)
 };
+
+constexpr int EOS_CS = 0;
+constexpr int EOS_VDW = 1;
+constexpr int EOS_PR = 2;
+constexpr int PSI_EXP = 3;
 
 // One CTA's piece of work: a tile of lattice `lat` with origin (x0, y0).
 struct Tile {
@@ -88,10 +96,33 @@ __device__ __forceinline__ double psi_bracket_fp64(double rho, double RT, double
     return RT * (num / (om * om * om)) - a * rho - cs2;
 }
 
+// p / rho - c_s^2 of the van der Waals (d = 1) or Peng-Robinson EOS, with
+// om = 1 - b rho (the pole at b rho = 1) and a the attraction (a alpha for PR).
+__device__ __forceinline__ double bracket_cubic_fp64(double rho, double RT, double a, double b, double cs2,
+                                                     bool pr) {
+    const double om = 1.0 - b * rho;
+    const double att = pr ? a * rho / (1.0 + b * rho * (2.0 - b * rho)) : a * rho;
+    return RT / om - att - cs2;
+}
+
+// psi of Eq. 12: exp(-1/rho) (eps = 0) or (rho / (eps + rho))^(1/eps).
+__device__ __forceinline__ double psi_exp_fp64(double rho, double eps, double inv_eps) {
+    return eps == 0.0 ? exp(-1.0 / rho) : exp(log(rho / (eps + rho)) * inv_eps);
+}
+
 __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsigned& flag) {
-    double q = psi_bracket_fp64(rho, P.RT, P.a, P.b4, P.cs2);
+    if (P.eos == PSI_EXP) {
+        if (!(rho > 0.0 && rho < 1.0e300)) {
+            flag |= FLAG_NONFINITE;
+            return 0.0;
+        }
+        return psi_exp_fp64(rho, P.eps12, P.inv_eps12);
+    }
+    const bool cubic = P.eos != EOS_CS;
+    double q = cubic ? bracket_cubic_fp64(rho, P.RT, P.a, P.b1, P.cs2, P.eos == EOS_PR)
+                     : psi_bracket_fp64(rho, P.RT, P.a, P.b4, P.cs2);
     double psi2 = P.kpsi * rho * q;
-    const bool dense_ok = (1.0 - P.b4 * rho) > 0.0;
+    const bool dense_ok = (cubic ? 1.0 - P.b1 * rho : 1.0 - P.b4 * rho) > 0.0;
     if (!(psi2 >= 0.0 && dense_ok)) {
         flag |= (psi2 < 0.0 && dense_ok) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
         psi2 = 0.0;
@@ -391,6 +422,43 @@ __device__ __forceinline__ V vpsi(V rho, const Phys<float>& P, unsigned& flag) {
         }
         set_lane(out, i, sqrt_approx(p2));
     }
+    return out;
+}
+
+// psi for the EOS other than Carnahan-Starling, one lane at a time (general
+// path only): van der Waals and Peng-Robinson through Eq. 13 with the same
+// FP64 fallback near the psi = 0 root and the same flags as vpsi, Eq. 12 by
+// expf/logf.
+__device__ __forceinline__ float psi_variant(float rho, const Phys<float>& P, unsigned& flag) {
+    if (P.eos == PSI_EXP) {
+        if (!(rho > 0.0f && rho <= 3.0e38f)) {
+            flag |= FLAG_NONFINITE;
+            return 0.0f;
+        }
+        return P.eps12 == 0.0f ? expf(-1.0f / rho) : expf(logf(rho / (P.eps12 + rho)) * P.inv_eps12);
+    }
+    const bool pr = P.eos == EOS_PR;
+    const float om = 1.0f - P.b1 * rho;
+    const float att = pr ? P.a * rho / fmaf(P.b1 * rho, 2.0f - P.b1 * rho, 1.0f) : P.a * rho;
+    const float q = P.RT / om - att - P.cs2;
+    float p2 = P.kpsi * rho * q;
+    if (fabsf(q) < 0.0078125f * P.cs2)
+        p2 = (float)((double)P.kpsi * (double)rho *
+                     bracket_cubic_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b1, (double)P.cs2, pr));
+    if (!(p2 >= 0.0f && p2 <= 3.0e38f && om > 0.0f)) {
+        flag |= (p2 < 0.0f && om > 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
+        p2 = 0.0f;
+    }
+    return sqrt_approx(p2);
+}
+
+// psi of any kind: the paired Carnahan-Starling form, else lane by lane.
+template <class V>
+__device__ __forceinline__ V vpsi_any(V rho, const Phys<float>& P, unsigned& flag) {
+    if (P.eos == EOS_CS) return vpsi(rho, P, flag);
+    V out;
+#pragma unroll
+    for (int i = 0; i < lanes(V{}); ++i) set_lane(out, i, psi_variant(lane(rho, i), P, flag));
     return out;
 }
 

@@ -65,7 +65,7 @@ __device__ __forceinline__ void f32_rho_psi(const float (&f)[RY][9], const bool 
                 v[a].v = make_float2(live[r] ? f[r][a] : 0.0f, live[r + 1] ? f[r + 1][a] : 0.0f);
             const F2 d = vsum9(v);
             const F2 rh = splat<F2>(rho_ref) + d;
-            const F2 ps = vpsi(rh, P, flag);
+            const F2 ps = vpsi_any(rh, P, flag);
             drho[r] = d.v.x;
             drho[r + 1] = d.v.y;
             rho[r] = rh.v.x;
@@ -81,7 +81,7 @@ __device__ __forceinline__ void f32_rho_psi(const float (&f)[RY][9], const bool 
             for (int a = 0; a < 9; ++a) v[a].v = live[r] ? f[r][a] : 0.0f;
             const F1 d = vsum9(v);
             const F1 rh = splat<F1>(rho_ref) + d;
-            const F1 ps = vpsi(rh, P, flag);
+            const F1 ps = vpsi_any(rh, P, flag);
             drho[r] = d.v;
             rho[r] = rh.v;
             psi[r] = live[r] ? ps.v : -1.0f;
@@ -89,13 +89,19 @@ __device__ __forceinline__ void f32_rho_psi(const float (&f)[RY][9], const bool 
     }
 }
 
-// psi of one halo cell from its pulled populations
+// psi of one halo cell from its pulled populations (ANY: every EOS kind;
+// else the Carnahan-Starling form the fast paths are restricted to)
+template <bool ANY = true>
 __device__ __forceinline__ float f32_halo_psi(const float (&fh)[9], float rho_ref, const Phys<float>& P,
                                               unsigned& flag) {
     F1 v[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) v[a].v = fh[a];
-    return vpsi(splat<F1>(rho_ref) + vsum9(v), P, flag).v;
+    const F1 rho = splat<F1>(rho_ref) + vsum9(v);
+    if constexpr (ANY)
+        return vpsi_any(rho, P, flag).v;
+    else
+        return vpsi(rho, P, flag).v;
 }
 
 // psi of the 8 neighbours of the node at s_psi index c (row stride SW), with
@@ -296,7 +302,7 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
             hc[k] = cy * SW + cx;
             float fh[9];
             pull_node<float>(fin, nullptr, plane, pitch, node_index(g, tile.x0 - 1 + cx, tile.y0 - 1 + cy), fh);
-            ph[k] = f32_halo_psi(fh, rho_ref, P, flag);
+            ph[k] = f32_halo_psi<false>(fh, rho_ref, P, flag);
         }
     }
 
@@ -465,7 +471,8 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
         Pp = A.phys + tile.lat;
     const Phys<T>& P = *Pp;
     if constexpr (std::is_same<T, float>::value && RY % 2 == 0) {
-        if (!g.has_mask && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4) {
+        if (!g.has_mask && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4 &&
+            P.eos == EOS_CS) {
             f32_tile_fast<TX, TYT, RY>(A, tile, g, P, s_psi);
             return;
         }

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
         const F2 psi = vpsi(rho, P, flag);
         s_psi[(ly0 + 1) * SW + lx + 1] = psi.v.x;
         s_psi[(ly0 + 2) * SW + lx + 1] = psi.v.y;
-        if (has_h) s_psi[hc] = f32_halo_psi(fh, rho_ref, P, flag);
+        if (has_h) s_psi[hc] = f32_halo_psi<false>(fh, rho_ref, P, flag);
         __syncthreads();
         if (flag) atomicOr(&A.status[T.lat], flag);
 

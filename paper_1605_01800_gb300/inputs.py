@@ -127,6 +127,8 @@ class LatticeSpec:
     R: float = 1.0
     G: float = -1.0
     meta: dict = field(default_factory=dict)
+    eos: str = "cs"                       # psi: "cs" (Eq. 13 with Eq. 15), "vdw", "pr" (Eq. 13), "psi_exp" (Eq. 12)
+    omega: float = 0.0                    # Peng-Robinson acentric factor
 
     @property
     def nodes(self) -> int:

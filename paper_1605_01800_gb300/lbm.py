@@ -49,9 +49,14 @@ class LbmError(RuntimeError):
         self.code = code
 
 
+LBM_EOS_CS, LBM_EOS_VDW, LBM_EOS_PR, LBM_PSI_EXP = 0, 1, 2, 3
+EOS_KINDS = {"cs": LBM_EOS_CS, "vdw": LBM_EOS_VDW, "pr": LBM_EOS_PR, "psi_exp": LBM_PSI_EXP}
+
+
 class lbm_eos_params(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
-                ("T", ctypes.c_double), ("G", ctypes.c_double)]
+                ("T", ctypes.c_double), ("G", ctypes.c_double), ("kind", ctypes.c_int),
+                ("omega", ctypes.c_double)]
 
 
 class lbm_lattice_desc(ctypes.Structure):
@@ -282,7 +287,8 @@ def make_desc(spec) -> lbm_lattice_desc:
     kept alive by the caller until lbm_create_batch returns)."""
     d = lbm_lattice_desc()
     d.nx, d.ny = spec.nx, spec.ny
-    d.eos = lbm_eos_params(spec.a, spec.b, spec.R, spec.T, spec.G)
+    d.eos = lbm_eos_params(spec.a, spec.b, spec.R, spec.T, spec.G, EOS_KINDS[getattr(spec, "eos", "cs")],
+                           getattr(spec, "omega", 0.0))
     d.s = (ctypes.c_double * 9)(*spec.s)
     d.eps = spec.eps
     d.rho_ref = spec.rho_ref

@@ -8,7 +8,7 @@ from paper_1605_01800_gb300 import inputs
 
 def oracle_from_spec(spec) -> d2q9.Lattice:
     L = d2q9.Lattice(spec.nx, spec.ny, a=spec.a, b=spec.b, R=spec.R, T=spec.T, G=spec.G,
-                     s=spec.s, eps=spec.eps, solid=spec.solid)
+                     s=spec.s, eps=spec.eps, solid=spec.solid, eos=spec.eos, omega=spec.omega)
     L.init(spec.rho)
     return L
 
