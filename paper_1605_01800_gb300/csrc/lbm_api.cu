@@ -323,16 +323,40 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     std::vector<Tile> tiles;
     std::vector<FastTile> fast;
     for (int l = 0; l < c->n; ++l) {
-        const Geom& g = c->lats[l].geom;
+        const HostLattice& L = c->lats[l];
+        const Geom& g = L.geom;
+        // solid cells of the periodic lattice summed over rectangles: a tile
+        // whose cells and two-cell frame hold none takes the wall-free paths
+        const int ex = g.nx + 4, ey = g.ny + 4;
+        std::vector<int> sat;
+        if (g.has_mask) {
+            sat.assign((size_t)(ex + 1) * (ey + 1), 0);
+            for (int j = 0; j < ey; ++j)
+                for (int i = 0; i < ex; ++i) {
+                    const int xs = ((i - 2) % g.nx + g.nx) % g.nx, ys = ((j - 2) % g.ny + g.ny) % g.ny;
+                    sat[(size_t)(j + 1) * (ex + 1) + i + 1] = L.mask[(size_t)ys * g.nx + xs] +
+                                                              sat[(size_t)j * (ex + 1) + i + 1] +
+                                                              sat[(size_t)(j + 1) * (ex + 1) + i] -
+                                                              sat[(size_t)j * (ex + 1) + i];
+                }
+        }
         for (int y0 = 0; y0 < g.ny; y0 += ty)
             for (int x0 = 0; x0 < g.nx; x0 += tx) {
-                // the pipelined kernel takes full tiles of wall-free Carnahan-Starling lattices of at least 4 x 4
-                if (pipe && !g.has_mask && x0 + tx <= g.nx && y0 + ty <= g.ny && g.nx >= 4 && g.ny >= 4 &&
-                    c->lats[l].desc.eos.kind == LBM_EOS_CS) {
+                const bool full = x0 + tx <= g.nx && y0 + ty <= g.ny;
+                bool clear = !g.has_mask;
+                if (g.has_mask && full) {  // frame [x0 - 2, x0 + tx + 2) x [y0 - 2, y0 + ty + 2)
+                    const int i0 = x0, i1 = x0 + tx + 4, j0 = y0, j1 = y0 + ty + 4;
+                    const int n = sat[(size_t)j1 * (ex + 1) + i1] - sat[(size_t)j0 * (ex + 1) + i1] -
+                                  sat[(size_t)j1 * (ex + 1) + i0] + sat[(size_t)j0 * (ex + 1) + i0];
+                    clear = n == 0;
+                }
+                // the pipelined kernel takes full tiles clear of walls in Carnahan-Starling
+                // lattices of at least 4 x 4
+                if (pipe && clear && full && g.nx >= 4 && g.ny >= 4 && L.desc.eos.kind == LBM_EOS_CS) {
                     const int edge = x0 < 2 || x0 + tx > g.nx - 2 || y0 < 2 || y0 + ty > g.ny - 2;
                     fast.push_back(FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, edge, {0, 0}});
                 } else {
-                    tiles.push_back(Tile{l, x0, y0, 0});
+                    tiles.push_back(Tile{l, x0, y0, clear ? 1 : 0});
                 }
             }
     }

@@ -65,9 +65,11 @@ constexpr int EOS_VDW = 1;
 constexpr int EOS_PR = 2;
 constexpr int PSI_EXP = 3;
 
-// One CTA's piece of work: a tile of lattice `lat` with origin (x0, y0).
+// One CTA's piece of work: a tile of lattice `lat` with origin (x0, y0);
+// clear = 1 when neither the tile nor its two-cell frame holds a solid cell
+// (set by the host from the wall mask; always 1 without walls).
 struct Tile {
-    int lat, x0, y0, pad;
+    int lat, x0, y0, clear;
 };
 
 __device__ __forceinline__ int wrap_index(int i, int n) {

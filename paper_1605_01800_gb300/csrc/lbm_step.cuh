@@ -192,7 +192,8 @@ __device__ __forceinline__ void f32_collide_store(float (&f)[RY][9], const bool 
 }
 
 // ---- FP32 fast path: a tile that lies wholly inside a lattice of at least
-// 4 x 4 nodes without walls. Every own node and halo cell exists, so there
+// 4 x 4 nodes with no solid cell in the tile or its two-cell frame (every
+// tile of a wall-free lattice). Every own node and halo cell is fluid, so there
 // are no liveness tests; a thread's nodes stay in register pairs (F2) from
 // the loads to the stores, and the ghost images are written only by tiles
 // within two cells of an edge. The arithmetic is that of the general path
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
         Pp = A.phys + tile.lat;
     const Phys<T>& P = *Pp;
     if constexpr (std::is_same<T, float>::value && RY % 2 == 0) {
-        if (!g.has_mask && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4 &&
+        if (tile.clear && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4 &&
             P.eos == EOS_CS) {
             f32_tile_fast<TX, TYT, RY>(A, tile, g, P, s_psi);
             return;
