@@ -85,6 +85,7 @@ struct lbm_ctx {
     // pipelined variants: the full wall-free tiles go to the persistent
     // kernel (d_fast, n_fast, pipe_grid CTAs), the rest (d_tiles) to the plain
     // kernel of the same node tile
+    TileGeom* d_tgeo = nullptr;  // d_tiles with their lattices' geometry (plain kernel)
     FastTile* d_fast = nullptr;
     int n_fast = 0;
     int pipe_grid = 0;
@@ -238,6 +239,7 @@ void free_ctx(lbm_ctx* c) {
     for (int v = 0; v < lbm_ctx::kMaxTma; ++v)
         for (int b = 0; b < 2; ++b) delete c->h_maps[v][b];
     cudaFree(c->d_fast);
+    cudaFree(c->d_tgeo);
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
     cudaFree(c->d_scalar);
@@ -362,20 +364,29 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     }
     if (tiles.size() > (size_t)0x7fffffff || fast.size() > (size_t)0x7fffffff)
         return fail(LBM_EINVAL, "too many tiles");
+    std::vector<TileGeom> tgeo(tiles.size());
+    for (size_t k = 0; k < tiles.size(); ++k) tgeo[k] = TileGeom{c->lats[tiles[k].lat].geom, tiles[k]};
     Tile* d = nullptr;
+    TileGeom* dg = nullptr;
     FastTile* df = nullptr;
     int rc = 0;
     if (!tiles.empty()) rc = dev_alloc(c, &d, tiles.size() * sizeof(Tile));
+    if (!rc && !tiles.empty()) rc = dev_alloc(c, &dg, tgeo.size() * sizeof(TileGeom));
     if (!rc && !fast.empty()) rc = dev_alloc(c, &df, fast.size() * sizeof(FastTile));
     if (rc) {
         if (d) {
             cudaFree(d);
             c->device_bytes -= tiles.size() * sizeof(Tile);
         }
+        if (dg) {
+            cudaFree(dg);
+            c->device_bytes -= tgeo.size() * sizeof(TileGeom);
+        }
         return rc;
     }
     cudaError_t e = cudaSuccess;
     if (d) e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && dg) e = cudaMemcpy(dg, tgeo.data(), tgeo.size() * sizeof(TileGeom), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && df) e = cudaMemcpy(df, fast.data(), fast.size() * sizeof(FastTile), cudaMemcpyHostToDevice);
     int per_sm = 0, sms = 0, dev = 0;
     if (e == cudaSuccess && pipe) {
@@ -385,8 +396,9 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     }
     if (e != cudaSuccess || (pipe && per_sm < 1)) {
         cudaFree(d);
+        cudaFree(dg);
         cudaFree(df);
-        c->device_bytes -= tiles.size() * sizeof(Tile) + fast.size() * sizeof(FastTile);
+        c->device_bytes -= tiles.size() * (sizeof(Tile) + sizeof(TileGeom)) + fast.size() * sizeof(FastTile);
         return e != cudaSuccess ? cuda_fail(e, "tile list upload")
                                 : fail(LBM_ECUDA, "pipelined variant %d cannot be resident on this device", tile_index);
     }
@@ -394,11 +406,16 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         cudaFree(c->d_tiles);
         c->device_bytes -= (size_t)c->n_tiles * sizeof(Tile);
     }
+    if (c->d_tgeo) {
+        cudaFree(c->d_tgeo);
+        c->device_bytes -= (size_t)c->n_tiles * sizeof(TileGeom);
+    }
     if (c->d_fast) {
         cudaFree(c->d_fast);
         c->device_bytes -= (size_t)c->n_fast * sizeof(FastTile);
     }
     c->d_tiles = d;
+    c->d_tgeo = dg;
     c->n_tiles = (int)tiles.size();
     c->d_fast = df;
     c->n_fast = (int)fast.size();
@@ -440,7 +457,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
     cudaError_t e;
     if (c->precision == LBM_FP64) {
         StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
-                           (double*)c->f[1 - src], c->d_mask, c->d_status};
+                           (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
         e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
     } else if (is_pipe(c->tile_index)) {
         const int v = c->tile_index - pipe_first();
@@ -449,7 +466,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         e = launch_step_pipe(v, c->pipe_grid, pa, table, c->stream);
         if (e == cudaSuccess && c->n_tiles > 0) {
             StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
-                              (float*)c->f[1 - src], c->d_mask, c->d_status};
+                              (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
             e = launch_step_f32(pipe_plain_partner(v), c->n_tiles, a, c->h_table, c->stream);
         }
     } else if (c->tile_index >= kTileCount) {
@@ -459,7 +476,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         e = launch_step_tma(v, c->tma_grid[v], a, *c->h_maps[v][src], *c->h_table, c->stream);
     } else {
         StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
-                          (float*)c->f[1 - src], c->d_mask, c->d_status};
+                          (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
         e = launch_step_f32(c->tile_index, c->n_tiles, a, c->h_table, c->stream);
     }
     if (e != cudaSuccess || !c->has_tiny) return e;

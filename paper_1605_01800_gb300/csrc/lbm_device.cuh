@@ -72,6 +72,14 @@ struct Tile {
     int lat, x0, y0, clear;
 };
 
+// A tile with a copy of its lattice's geometry, so that a CTA learns both
+// with one round trip to memory (four independent 16-byte loads) instead of
+// a tile load followed by a dependent geometry load.
+struct alignas(16) TileGeom {
+    Geom g;
+    Tile t;
+};
+
 __device__ __forceinline__ int wrap_index(int i, int n) {
     int r = i % n;
     return r < 0 ? r + n : r;

@@ -44,6 +44,7 @@ struct StepArgs {
     T* fout;
     const uint8_t* mask;
     unsigned* status;
+    const TileGeom* tg;  // per entry of `tiles`: the tile and its lattice's geometry
 };
 
 // ---- FP32 node math shared by the plain-load and the TMA kernels: nodes are
@@ -461,8 +462,8 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
     constexpr int SH = TY + 2;
     __shared__ T s_psi[SH * SW];
 
-    const Tile tile = A.tiles[blockIdx.x];
-    const Geom g = A.geom[tile.lat];
+    const Tile tile = A.tg[blockIdx.x].t;
+    const Geom g = A.tg[blockIdx.x].g;  // independent of the tile load
     // restrict: the stores to fout cannot alias the parameters, so they need
     // not be reloaded after every store
     const Phys<T>* __restrict__ Pp;
