@@ -319,6 +319,8 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     if (tile_index < 0 || tile_index >= total_tiles()) return fail(LBM_EINVAL, "no tile shape %d", tile_index);
     if (tile_index >= kTileCount && c->precision == LBM_FP64)
         return fail(LBM_EINVAL, "tile %d is an FP32-only variant; this context stores FP64", tile_index);
+    if (is_tma(tile_index) && c->n > kTmaMaxLattices)  // refused before the current tile list is replaced
+        return fail(LBM_EINVAL, "tile %d (TMA) takes batches of at most %d lattices", tile_index, kTmaMaxLattices);
     const bool pipe = is_pipe(tile_index);
     int tx = 0, ty = 0;
     tile_shape(tile_index, &tx, &ty);
@@ -1037,7 +1039,16 @@ int lbm_set_tile(lbm_ctx* c, int index) {
         return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, total_tiles());
     if (index == c->tile_index) return LBM_OK;
     CK(cudaStreamSynchronize(c->stream));
-    return build_tiles(c, index);
+    const int prev = c->tile_index;
+    const int rc = build_tiles(c, index);
+    if (rc != LBM_OK && c->tile_index != prev) {
+        // a later stage failed after the list was replaced: go back to the
+        // previous shape, keeping the first error's message
+        const std::string msg = g_last_error;
+        build_tiles(c, prev);
+        g_last_error = msg;
+    }
+    return rc;
 }
 
 int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {

@@ -388,3 +388,31 @@ def test_laplace_slope_fp32_matches_fp64():
     assert f32["sigma"] == pytest.approx(f64["sigma"], rel=2e-3)
     for b32, b64 in zip(f32["bubbles"], f64["bubbles"]):
         assert b32["r"] == pytest.approx(b64["r"], rel=0.01)
+
+
+def test_batch_beyond_the_parameter_table_equals_individual_runs():
+    """More lattices than fit in the kernel-parameter table (64): parameters
+    come from global memory, TMA shapes are refused, every other shape gives
+    the same nodes as each lattice run alone."""
+    specs = [small_spec(16 + 8 * (i % 5), 12 + 4 * (i % 3), seed=100 + i, walls=(i % 7 == 0),
+                        tr=0.6 + 0.3 * (i % 4) / 3) for i in range(70)]
+    kinds = [lbm.lbm_tile_kind(t) for t in range(lbm.lbm_tile_count())]
+    b = lbm.Batch(specs, "fp32_dev")
+    for t, k in enumerate(kinds):
+        if k == lbm.LBM_TILE_TMA:
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_tile(b.ctx, t)
+            assert e.value.code == lbm.LBM_EINVAL
+    # the refused shapes left the context on its previous one: it still steps
+    b.init()
+    b.step(3)
+    (ref,) = run_gpu([specs[5]], "fp32_dev", 3)
+    for x, y in zip(b.moments(5), ref):
+        assert np.array_equal(x, y)
+    b.close()
+    for t in [0] + [t for t, k in enumerate(kinds) if k == lbm.LBM_TILE_PIPELINED][:1]:
+        batched = run_gpu(specs, "fp32_dev", 7, tile=t)
+        for i in (0, 7, 33, 69):
+            (alone,) = run_gpu([specs[i]], "fp32_dev", 7)
+            for x, y in zip(batched[i], alone):
+                assert np.array_equal(x, y), (t, i)
