@@ -20,7 +20,10 @@
  *     "_all" variants take the lattices of a batch concatenated in creation
  *     order (sum of nx*ny doubles).
  *   - Host pointers may be pageable or pinned; the library copies them
- *     (inputs) or fills them (outputs) and never keeps them.
+ *     (inputs) or fills them (outputs) and never keeps them. A page-locked
+ *     (cudaHostAlloc / cudaHostRegister) density array given to a
+ *     density-only lbm_read_moments* is written by the kernel in place, with
+ *     no staging copy; the call still returns only once it is complete.
  *   - Device memory is owned by the context and released by lbm_destroy().
  *   - Work is enqueued on the context's stream (lbm_set_stream). Entry points
  *     that return data to the host synchronise that stream.

@@ -563,6 +563,27 @@ long long range_nodes(lbm_ctx* c, int lat0, int n_lat) {
 
 // Initial state of lattices [lat0, lat0 + n_lat) from host arrays that start
 // at lattice lat0's first node: one upload per field, one kernel launch.
+// Device address under which kernels reach a page-locked, mapped host
+// buffer (memory from cudaHostAlloc / cudaHostRegister, e.g. a pinned torch
+// tensor), or null for pageable memory. The density read-out writes such a
+// buffer directly over the host link, with no staging copy.
+const void* mapped_device_ptr(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// `p` shifted back by `nodes` doubles: the base the kernels index by
+// geom.node_off when `p` holds the range starting at node `nodes`
+template <typename P>
+P* node_base(P* p, long long nodes) {
+    return p ? (P*)((uintptr_t)p - (uintptr_t)(nodes * (long long)sizeof(double))) : nullptr;
+}
+
 int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double* ux, const double* uy) {
     bool changed = false;
     for (int l = lat0; l < lat0 + n_lat; ++l) {
@@ -577,23 +598,25 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
     }
     const long long base = c->lats[lat0].geom.node_off;
     const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
+    // staged through the device buffer d_io: a bulk copy, then the init
+    // kernel (faster than the kernel reading a mapped host buffer in place,
+    // whose scattered reads each pay the host link's latency)
     double* d_rho = c->d_io + base;
     double* d_ux = ux ? c->d_io + c->total_nodes + base : nullptr;
     double* d_uy = uy ? c->d_io + 2 * c->total_nodes + base : nullptr;
     CK(cudaMemcpyAsync(d_rho, rho, bytes, cudaMemcpyHostToDevice, c->stream));
     if (ux) CK(cudaMemcpyAsync(d_ux, ux, bytes, cudaMemcpyHostToDevice, c->stream));
     if (uy) CK(cudaMemcpyAsync(d_uy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
+    const double* k_rho = c->d_io;
+    const double* k_ux = ux ? c->d_io + c->total_nodes : nullptr;
+    const double* k_uy = uy ? c->d_io + 2 * c->total_nodes : nullptr;
     const LaunchSet ls = launch_set(c, lat0, n_lat);
     CK(cudaMemsetAsync(c->d_bad, 0, c->n * sizeof(unsigned), c->stream));
     cudaError_t e;
     if (c->precision == LBM_FP64)
-        e = launch_init_f64(ls, c->d_io, ux ? c->d_io + c->total_nodes : nullptr,
-                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (double*)c->f[c->cur], c->d_bad,
-                            c->stream);
+        e = launch_init_f64(ls, k_rho, k_ux, k_uy, (double*)c->f[c->cur], c->d_bad, c->stream);
     else
-        e = launch_init_f32(ls, c->d_io, ux ? c->d_io + c->total_nodes : nullptr,
-                            uy ? c->d_io + 2 * c->total_nodes : nullptr, (float*)c->f[c->cur], c->d_bad,
-                            c->stream);
+        e = launch_init_f32(ls, k_rho, k_ux, k_uy, (float*)c->f[c->cur], c->d_bad, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     c->launches += 1;
     if (c->has_tiny) {  // lattices under 4 cells: their ghost frames are written separately
@@ -622,10 +645,18 @@ int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, doub
     double* d[4] = {c->d_io, c->d_io + N, c->d_io + 2 * N, c->d_io + 3 * N};
     const LaunchSet ls = launch_set(c, lat0, n_lat);
     cudaError_t e;
-    if (!ux && !uy && !p) {  // density only: one light kernel
-        e = c->precision == LBM_FP64 ? launch_density_f64(ls, (const double*)c->f[c->cur], d[0], c->stream)
-                                     : launch_density_f32(ls, (const float*)c->f[c->cur], d[0], c->stream);
+    const long long base = c->lats[lat0].geom.node_off;
+    double* m_rho = (double*)mapped_device_ptr(rho);
+    if (!ux && !uy && !p) {  // density only: one light kernel, writing a mapped host buffer in place
+        double* out = m_rho ? node_base(m_rho, base) : d[0];
+        e = c->precision == LBM_FP64 ? launch_density_f64(ls, (const double*)c->f[c->cur], out, c->stream)
+                                     : launch_density_f32(ls, (const float*)c->f[c->cur], out, c->stream);
         c->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
+        if (m_rho) {
+            CK(cudaStreamSynchronize(c->stream));
+            return LBM_OK;
+        }
     } else {
         e = c->precision == LBM_FP64
                 ? launch_moments_f64(ls, (const double*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream)
@@ -633,7 +664,6 @@ int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, doub
         c->launches += 2;
     }
     if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
-    const long long base = c->lats[lat0].geom.node_off;
     const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
     double* h[4] = {rho, ux, uy, p};
     for (int k = 0; k < 4; ++k)

@@ -416,3 +416,31 @@ def test_batch_beyond_the_parameter_table_equals_individual_runs():
             (alone,) = run_gpu([specs[i]], "fp32_dev", 7)
             for x, y in zip(batched[i], alone):
                 assert np.array_equal(x, y), (t, i)
+
+
+def test_pinned_host_buffers_are_read_and_written_in_place():
+    """Page-locked host arrays (here pinned torch tensors) are written by the
+    density read-out directly; the results equal those through pageable
+    arrays (staged copies), bit for bit, for the whole batch and for one
+    lattice, and pinned inputs give the same state as pageable ones."""
+    torch = pytest.importorskip("torch")
+    specs = [small_spec(48, 40, walls=True, seed=41), small_spec(33, 17, seed=42), small_spec(64, 32, seed=43)]
+    n = sum(s.nodes for s in specs)
+    rho_pageable = np.concatenate([s.rho.ravel() for s in specs])
+    rho_pinned = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    rho_pinned[:] = rho_pageable
+    out = {}
+    for kind, src in (("pageable", rho_pageable), ("pinned", rho_pinned)):
+        b = lbm.Batch(specs, "fp32_dev")
+        lbm.lbm_init_fields_all(b.ctx, src)
+        b.step(4)
+        dst = np.empty(n) if kind == "pageable" else torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        lbm.lbm_read_moments_all(b.ctx, dst)
+        one = np.empty(specs[2].nodes) if kind == "pageable" else \
+            torch.empty(specs[2].nodes, dtype=torch.float64, pin_memory=True).numpy()
+        lbm.lbm_read_moments(b.ctx, 2, one)
+        out[kind] = (dst.copy(), one.copy())
+        b.close()
+    assert np.array_equal(out["pageable"][0], out["pinned"][0])
+    assert np.array_equal(out["pageable"][1], out["pinned"][1])
+    assert np.array_equal(out["pinned"][1], out["pinned"][0][-specs[2].nodes:])
