@@ -110,6 +110,7 @@ struct lbm_ctx {
     double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
     double* d_psi = nullptr;     // read-out scratch: one ghosted FP64 plane per lattice
     unsigned* d_bad = nullptr;   // per-lattice invalid-input flags of the init kernel
+    unsigned* h_bad = nullptr;   // their page-locked host copy
     std::vector<Phys<double>> phys_d;
     PhysTable<float>* h_table = nullptr;  // FP32 parameters as a kernel argument (n <= kParamLattices)
     size_t device_bytes = 0;
@@ -246,6 +247,7 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->d_io);
     cudaFree(c->d_psi);
     cudaFree(c->d_bad);
+    cudaFreeHost(c->h_bad);
     delete c;
 }
 
@@ -627,11 +629,10 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
     }
     // the host arrays may be pageable and the staging buffer is reused: wait,
     // then report invalid input found by the init kernel
-    std::vector<unsigned> bad(c->n, 0u);
-    CK(cudaMemcpyAsync(bad.data(), c->d_bad, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_bad, c->d_bad, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int l = lat0; l < lat0 + n_lat; ++l)
-        if (bad[l])
+        if (c->h_bad[l])
             return fail(LBM_EINVAL,
                         "lattice %d: a fluid density is not finite and > 0, or a velocity is not finite "
                         "(the lattice's state is undefined until the next successful init)", l);
@@ -758,6 +759,11 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->total_nodes * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_psi, ((size_t)c->total_elems / 9 + 64) * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_bad, n * sizeof(unsigned));
+    if (!rc && cudaHostAlloc((void**)&c->h_bad, n * sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_bad = nullptr;
+        rc = fail(LBM_ENOMEM, "cudaHostAlloc(%zu bytes) failed", n * sizeof(unsigned));
+    }
     if (rc) {
         free_ctx(c);
         return rc;

@@ -73,13 +73,16 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
     if (invalid) atomicOr(&bad[lat], 1u);
 }
 
-// Pulled distribution of node (x, y) as FP64 full populations; false if solid.
+// Pulled distribution of node (x, y) as stored (f_a - w_a rho_ref, or f_a
+// for plain storage), in FP64; false if solid. The density is rho_ref plus
+// their sum (the weights sum to 1) and the momentum their first moment (the
+// w_a rho_ref parts cancel), so the read-outs need no per-population FMA.
 template <typename T>
-__device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask,
-                                            double rho_ref, int x, int y, double out[9]) {
+__device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask, int x, int y,
+                                            double out[9]) {
     T tmp[9];
     if (pull_node<T>(f, mask, (int)g.plane, g.pitch, node_index(g, x, y), tmp)) return false;
-    for (int a = 0; a < 9; ++a) out[a] = (double)tmp[a] + kWeq[a] * rho_ref;
+    for (int a = 0; a < 9; ++a) out[a] = (double)tmp[a];
     return true;
 }
 
@@ -110,7 +113,7 @@ __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<do
         const int x = (int)(i % w) - 1, y = (int)(i / w) - 1;
         double fc[9];
         const int c = node_index(g, x, y);
-        if (!pulled_fp64<T>(g, f, mask, P.rho_ref, x, y, fc)) {
+        if (!pulled_fp64<T>(g, f, mask, x, y, fc)) {
             psi_plane[c] = -1.0;
             if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
                 const long long o = g.node_off + (long long)y * g.nx + x;
@@ -120,7 +123,7 @@ __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<do
             }
             continue;
         }
-        double rho = 0.0, jx = 0.0, jy = 0.0;
+        double rho = P.rho_ref, jx = 0.0, jy = 0.0;
         for (int a = 0; a < 9; ++a) {
             rho += fc[a];
             jx += kEx[a] * fc[a];
@@ -153,8 +156,10 @@ __global__ void density_kernel(const Geom* __restrict__ geoms, const Phys<double
         const int y = i / g.nx, x = i - y * g.nx;
         double fc[9];
         double rho = 0.0;
-        if (pulled_fp64<T>(g, f, mask, rho_ref, x, y, fc))
+        if (pulled_fp64<T>(g, f, mask, x, y, fc)) {
+            rho = rho_ref;
             for (int a = 0; a < 9; ++a) rho += fc[a];
+        }
         rho_out[g.node_off + i] = rho;
     }
 }
