@@ -462,6 +462,13 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
     constexpr int SH = TY + 2;
     __shared__ T s_psi[SH * SW];
 
+    // CTA b asks L2 for line b of the tile records, so that the CTAs of
+    // later waves find theirs there instead of in DRAM
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const int nl = (int)((gridDim.x * sizeof(TileGeom) + 127) / 128);
+        if ((int)blockIdx.x < nl)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)A.tg + 128 * (size_t)blockIdx.x));
+    }
     const Tile tile = A.tg[blockIdx.x].t;
     const Geom g = A.tg[blockIdx.x].g;  // independent of the tile load
     // restrict: the stores to fout cannot alias the parameters, so they need
