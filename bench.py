@@ -360,6 +360,22 @@ def main():
     fp64_mlups = nodes / (fp64_ms * 1e-3) / 1e6
     b64.close()
 
+    # ---- the error that goes with the FP32 number: fresh FP32 and FP64 runs
+    # of the same batch for the same steps, densities compared node by node
+    acc_steps = 500
+    rho = {}
+    for prec in ("fp32_dev", "fp64"):
+        ba = lbm.Batch(specs, prec, stream=stream)
+        ba.init()
+        ba.step(acc_steps)
+        out = np.empty(nodes)
+        lbm.lbm_read_moments_all(ba.ctx, out)
+        rho[prec] = out
+        ba.close()
+    acc = {"steps": acc_steps, "max_rel_rho": float(np.max(np.abs(rho["fp32_dev"] / rho["fp64"] - 1.0))),
+           "mean_rel_rho": float(np.mean(np.abs(rho["fp32_dev"] / rho["fp64"] - 1.0))),
+           "note": "FP32 deviation storage against FP64 storage, every node of the batch"}
+
     # ---- context: a plain device copy of the same bytes under the same flush
     src = torch.empty(nodes * 9, dtype=torch.float32, device=dev)
     dst = torch.empty_like(src)
@@ -421,6 +437,7 @@ def main():
         "copy_same_bytes": {"achieved_gbs": copy_gbs, "ms": copy_ms, "frac": copy_gbs / peak,
                             "note": "torch device copy of 9 x 4 B per node, same flush"},
         "large_workloads": large,
+        "fp32_vs_fp64": acc,
         "fp64_plain": {"value": fp64_mlups, "unit": "MLUPS", "ms_per_step": fp64_ms, "steps": k64,
                        "achieved_gbs": ALG_BYTES_FP64 * nodes / (fp64_ms * 1e-3) / 1e9},
         "l2_resident": {"value": l2_mlups, "unit": "MLUPS",
