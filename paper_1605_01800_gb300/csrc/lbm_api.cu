@@ -102,6 +102,10 @@ struct lbm_ctx {
     // every copy does land) and the step reports LBM_ETIMEOUT without a fault.
     long long tma_wait_limit = 2000000000LL;
     unsigned tma_extra_tx = 0;
+    // LBM_FAIL_ALLOC_AT=k (read at creation) makes the k-th device allocation
+    // of the context fail as if the device were out of memory, so that a test
+    // can check the error path and the clean-up without exhausting a GPU
+    long long fail_alloc_at = 0, alloc_count = 0;
     int tile_index = 0;
     bool has_tiny = false;       // a lattice under 4 cells in x or y (see launch_one_step)
     unsigned* d_status = nullptr;
@@ -208,6 +212,10 @@ void to_float(const Phys<double>& D, Phys<float>& F) {
 
 template <typename P>
 int dev_alloc(lbm_ctx* c, P** ptr, size_t bytes) {
+    if (c->fail_alloc_at > 0 && ++c->alloc_count == c->fail_alloc_at) {  // injected failure (tests)
+        *ptr = nullptr;
+        return fail(LBM_ENOMEM, "cudaMalloc(%zu bytes): injected failure (LBM_FAIL_ALLOC_AT)", bytes);
+    }
     cudaError_t e = cudaMalloc((void**)ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -694,6 +702,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     lbm_ctx* c = new lbm_ctx();
     if (const char* w = getenv("LBM_TMA_WAIT_CYCLES")) c->tma_wait_limit = std::max(0LL, atoll(w));
     if (const char* x = getenv("LBM_TMA_EXTRA_TX")) c->tma_extra_tx = (unsigned)std::min(4096LL, std::max(0LL, atoll(x)));
+    if (const char* a = getenv("LBM_FAIL_ALLOC_AT")) c->fail_alloc_at = std::max(0LL, atoll(a));
     c->n = n;
     c->precision = precision;
     c->elem = precision == LBM_FP64 ? 8 : 4;

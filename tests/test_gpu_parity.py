@@ -444,3 +444,62 @@ def test_pinned_host_buffers_are_read_and_written_in_place():
     assert np.array_equal(out["pageable"][0], out["pinned"][0])
     assert np.array_equal(out["pageable"][1], out["pinned"][1])
     assert np.array_equal(out["pinned"][1], out["pinned"][0][-specs[2].nodes:])
+
+
+@pytest.mark.parametrize("precision", ["fp32_dev", "fp64"])
+def test_y_uniform_batch_matches_one_row_lattice(precision):
+    """A y-uniform field on 64 x 8 (main kernels, ghost images in the step)
+    and on 64 x 1 (a lattice under 4 cells: frames rewritten by the refresh
+    kernel) must evolve identically, row for row, bit for bit."""
+    Tc = inputs.critical_temperature()
+    c = inputs.coexistence(0.7)
+    nx = 64
+    x = np.arange(nx, dtype=float)
+    prof = c["rho_g"] + 0.5 * (c["rho_l"] - c["rho_g"]) * (np.tanh(2 * (x - 16) / 4) - np.tanh(2 * (x - 48) / 4))
+    specs = [inputs.LatticeSpec(nx, ny, 0.7 * Tc, inputs.relax_rates(0.7), 1.86, np.tile(prof, (ny, 1)),
+                                rho_ref=c["rho_g"]) for ny in (1, 8)]
+    (one, many) = run_gpu(specs, precision, 40)
+    for a, b in zip(one, many):
+        for row in b:
+            assert np.array_equal(row, a[0])
+
+
+def test_injected_allocation_failures_leave_nothing_broken(monkeypatch):
+    """Every device allocation of a context, made to fail in turn from the
+    host (LBM_FAIL_ALLOC_AT), is reported as LBM_ENOMEM. A context that
+    failed to build is cleaned up; one that built but failed to switch its
+    tile shape keeps the shape it had; both cases leave later contexts and
+    steps correct."""
+    specs = [small_spec(40, 24, walls=True, seed=51), small_spec(33, 17, seed=52)]
+    ref = run_gpu(specs, "fp32_dev", 3)
+    pipe = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_PIPELINED][0]
+    failed_create = failed_switch = 0
+    for k in range(1, 40):
+        monkeypatch.setenv("LBM_FAIL_ALLOC_AT", str(k))
+        try:
+            b = lbm.Batch(specs, "fp32_dev")
+        except lbm.LbmError as e:
+            assert e.code == lbm.LBM_ENOMEM and "injected" in str(e)
+            failed_create += 1
+            continue
+        finally:
+            monkeypatch.delenv("LBM_FAIL_ALLOC_AT")
+        switched = True
+        try:
+            lbm.lbm_set_tile(b.ctx, pipe)
+        except lbm.LbmError as e:
+            assert e.code == lbm.LBM_ENOMEM and "injected" in str(e)
+            failed_switch += 1
+            switched = False
+        b.init()
+        b.step(3)
+        for i in range(len(specs)):
+            for x, y in zip(b.moments(i), ref[i]):
+                assert np.array_equal(x, y)
+        b.close()
+        if switched:
+            break
+    assert failed_create >= 10 and failed_switch >= 1
+    (again,) = run_gpu(specs[:1], "fp32_dev", 3)
+    for x, y in zip(again, ref[0]):
+        assert np.array_equal(x, y)

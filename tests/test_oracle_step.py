@@ -283,3 +283,26 @@ def test_flat_interface_li_term_matches_eq9():
     rg, rl, _ = _slab(0.7, 1.0, 0.6, steps=60000)
     assert rg == pytest.approx(rg9, rel=0.02)
     assert rl == pytest.approx(rl9, rel=5e-4)
+
+
+def test_y_uniform_field_evolves_as_the_one_row_lattice():
+    # A field that depends on x only stays y-uniform, and each of its rows
+    # equals the run of the same row alone on an nx x 1 periodic lattice
+    # (there every y-neighbour is the node itself): bit for bit, since every
+    # node sees the same operands in the same order.
+    Tc, _, _ = thermo.critical_point()
+    rg, rl, _ = thermo.maxwell(0.7 * Tc)
+    nx = 64
+    x = np.arange(nx, dtype=float)
+    prof = rg + 0.5 * (rl - rg) * (np.tanh(2 * (x - 16) / 4) - np.tanh(2 * (x - 48) / 4))
+    ux = 0.01 * np.sin(2 * np.pi * x / nx)
+    s = [1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1 / 0.7, 1 / 0.7]
+    runs = []
+    for ny in (1, 6):
+        L = d2q9.Lattice(nx, ny, T=0.7 * Tc, s=s, eps=1.86)
+        L.init(np.tile(prof, (ny, 1)), np.tile(ux, (ny, 1)), np.zeros((ny, nx)))
+        L.step(50)
+        runs.append(L.moments())
+    for a, b in zip(runs[0], runs[1]):
+        for row in b:
+            assert np.array_equal(row, a[0])
