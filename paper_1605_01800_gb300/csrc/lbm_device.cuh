@@ -145,6 +145,33 @@ __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsi
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Population and mask accesses of the step. Debug builds (-DLBM_DEBUG)
+// check each index against the lattice's nine planes (one plane for the
+// mask): an index outside reads NaN (a population) or solid (the mask) and a
+// store outside is skipped, so a wrong offset shows up as a wrong or
+// non-finite result in the parity tests instead of touching memory that
+// belongs to another lattice. Release builds access directly.
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T* __restrict__ p, int i, int n) {
+#ifdef LBM_DEBUG
+    if (i < 0 || i >= n) return T(NAN);
+#endif
+    return p[i];
+}
+template <typename T>
+__device__ __forceinline__ void st_pop(T* __restrict__ p, int i, int n, T v) {
+#ifdef LBM_DEBUG
+    if (i < 0 || i >= n) return;
+#endif
+    p[i] = v;
+}
+__device__ __forceinline__ uint8_t ld_mask(const uint8_t* __restrict__ m, int i, int n) {
+#ifdef LBM_DEBUG
+    if (i < 0 || i >= n) return 1;
+#endif
+    return m[i];
+}
+
 // Gather the distribution of the cell at stored index c after streaming
 // (Eq. 5) from the post-collision array `fin` (pull form):
 // f_a(x) = f*_a(x - e_a); periodic images come from the ghost frame, so c may
@@ -154,28 +181,31 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 template <typename T>
 __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8_t* __restrict__ mask,
                                           int plane, int pitch, int c, T f[9]) {
+    const int np = 9 * plane;  // < 2^31 (checked when the lattice is created)
+    auto F = [&](int a, int i) { return ld_pop<T>(fin, a * plane + i, np); };
     if (mask != nullptr) {
-        if (mask[c]) return true;
-        f[0] = fin[c];
-        f[1] = mask[c - 1]         ? fin[3 * plane + c] : fin[1 * plane + c - 1];
-        f[2] = mask[c - pitch]     ? fin[4 * plane + c] : fin[2 * plane + c - pitch];
-        f[3] = mask[c + 1]         ? fin[1 * plane + c] : fin[3 * plane + c + 1];
-        f[4] = mask[c + pitch]     ? fin[2 * plane + c] : fin[4 * plane + c + pitch];
-        f[5] = mask[c - pitch - 1] ? fin[7 * plane + c] : fin[5 * plane + c - pitch - 1];
-        f[6] = mask[c - pitch + 1] ? fin[8 * plane + c] : fin[6 * plane + c - pitch + 1];
-        f[7] = mask[c + pitch + 1] ? fin[5 * plane + c] : fin[7 * plane + c + pitch + 1];
-        f[8] = mask[c + pitch - 1] ? fin[6 * plane + c] : fin[8 * plane + c + pitch - 1];
+        auto M = [&](int i) { return ld_mask(mask, i, plane); };
+        if (M(c)) return true;
+        f[0] = F(0, c);
+        f[1] = M(c - 1)         ? F(3, c) : F(1, c - 1);
+        f[2] = M(c - pitch)     ? F(4, c) : F(2, c - pitch);
+        f[3] = M(c + 1)         ? F(1, c) : F(3, c + 1);
+        f[4] = M(c + pitch)     ? F(2, c) : F(4, c + pitch);
+        f[5] = M(c - pitch - 1) ? F(7, c) : F(5, c - pitch - 1);
+        f[6] = M(c - pitch + 1) ? F(8, c) : F(6, c - pitch + 1);
+        f[7] = M(c + pitch + 1) ? F(5, c) : F(7, c + pitch + 1);
+        f[8] = M(c + pitch - 1) ? F(6, c) : F(8, c + pitch - 1);
         return false;
     }
-    f[0] = fin[c];
-    f[1] = fin[1 * plane + c - 1];
-    f[2] = fin[2 * plane + c - pitch];
-    f[3] = fin[3 * plane + c + 1];
-    f[4] = fin[4 * plane + c + pitch];
-    f[5] = fin[5 * plane + c - pitch - 1];
-    f[6] = fin[6 * plane + c - pitch + 1];
-    f[7] = fin[7 * plane + c + pitch + 1];
-    f[8] = fin[8 * plane + c + pitch - 1];
+    f[0] = F(0, c);
+    f[1] = F(1, c - 1);
+    f[2] = F(2, c - pitch);
+    f[3] = F(3, c + 1);
+    f[4] = F(4, c + pitch);
+    f[5] = F(5, c - pitch - 1);
+    f[6] = F(6, c - pitch + 1);
+    f[7] = F(7, c + pitch + 1);
+    f[8] = F(8, c + pitch - 1);
     return false;
 }
 
@@ -200,7 +230,7 @@ __device__ __forceinline__ void store_ghost_images(T* __restrict__ base, const G
         for (int i = 0; i < nxs; ++i) {
             if (i == 0 && j == 0) continue;
             const int c = node_index(g, xs[i], ys[j]);
-            for (int a = 0; a < 9; ++a) base[a * g.plane + c] = v[a];
+            for (int a = 0; a < 9; ++a) st_pop<T>(base, (int)(a * g.plane + c), (int)(9 * g.plane), v[a]);
         }
 }
 
@@ -218,14 +248,14 @@ __device__ __forceinline__ void store_images(T* __restrict__ base, const Geom& g
     const int dy = !ey ? 0 : (y < 2 ? g.ny : -g.ny) * g.pitch;
     if (dx != 0) {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) base[a * plane + c + dx] = v[a];
+        for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c + dx, 9 * plane, v[a]);
     }
     if (dy != 0) {
 #pragma unroll
-        for (int a = 0; a < 9; ++a) base[a * plane + c + dy] = v[a];
+        for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c + dy, 9 * plane, v[a]);
         if (dx != 0) {
 #pragma unroll
-            for (int a = 0; a < 9; ++a) base[a * plane + c + dx + dy] = v[a];
+            for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c + dx + dy, 9 * plane, v[a]);
         }
     }
 }
@@ -236,7 +266,7 @@ __device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, 
     const int c = node_index(g, x, y);
     const int plane = (int)g.plane;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) base[a * plane + c] = v[a];
+    for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c, 9 * plane, v[a]);
     // lattices under 4 cells in x or y can have several images per node;
     // their frames are rewritten by ghost_refresh_kernel after each step
     if (g.nx < 4 || g.ny < 4) return;

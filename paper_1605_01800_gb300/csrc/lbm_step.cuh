@@ -203,7 +203,8 @@ __device__ __forceinline__ void f32_collide_store(float (&f)[RY][9], const bool 
 // the nine pulled populations of the vertically adjacent nodes at stored
 // indices c and c + pitch, as pairs (no walls)
 __device__ __forceinline__ void pull_pair(const float* __restrict__ fin, int plane, int pitch, int c, F2 f[9]) {
-    auto ld2 = [&](int i) { return F2{make_float2(fin[i], fin[i + pitch])}; };
+    const int np = 9 * plane;
+    auto ld2 = [&](int i) { return F2{make_float2(ld_pop(fin, i, np), ld_pop(fin, i + pitch, np))}; };
     f[0] = ld2(c);
     f[1] = ld2(1 * plane + c - 1);
     f[2] = ld2(2 * plane + c - pitch);
@@ -234,8 +235,8 @@ __device__ __forceinline__ void f32_pair_finish(F2 (&f)[9], F2 rho, F2 drho, F2 
     vcollide(f, rho, drho, Fx, Fy, g2G2, P);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        fo[a * plane + cs] = f[a].v.x;
-        fo[a * plane + cs + pitch] = f[a].v.y;
+        st_pop(fo, a * plane + cs, 9 * plane, f[a].v.x);
+        st_pop(fo, a * plane + cs + pitch, 9 * plane, f[a].v.y);
     }
     if (edge) {
         float v0[9], v1[9];
@@ -461,6 +462,12 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
     __shared__ T s_psi[SH * SW];
+#ifdef LBM_DEBUG
+    // debug builds poison the psi tile, so a cell that no thread writes shows
+    // up as NaN in the result
+    for (int i = threadIdx.y * TX + threadIdx.x; i < SH * SW; i += TX * TYT) s_psi[i] = T(NAN);
+    __syncthreads();
+#endif
 
     // CTA b asks L2 for line b of the tile records, so that the CTAs of
     // later waves find theirs there instead of in DRAM

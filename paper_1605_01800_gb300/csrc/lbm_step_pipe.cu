@@ -57,6 +57,11 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
         const bool more = tn < A.n_fast;
         FastTile Tn;
         if (more) Tn = A.fast[tn];
+#ifdef LBM_DEBUG
+        // debug builds poison the psi tile of every tile (see step_kernel)
+        for (int i = tid; i < SH * SW; i += NT) s_psi[i] = NAN;
+        __syncthreads();
+#endif
         const Phys<float>* __restrict__ Pp;
         if constexpr (TABLE)
             Pp = &PT.p[T.lat];

@@ -80,16 +80,21 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.environ.get("LBM_LIBRARY") or _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load liblbm.so (building it first if allowed and needed)."""
+    """Load liblbm.so (building it first if allowed and needed). The
+    environment variable LBM_LIBRARY names another build of it to load
+    instead, e.g. the debug build (build.DEBUG_LIB), which must exist."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if not os.path.exists(path) or not _build.up_to_date():
+    path = library_path()
+    if os.environ.get("LBM_LIBRARY"):
+        if not os.path.exists(path):
+            raise RuntimeError(f"LBM_LIBRARY={path} does not exist")
+    elif not os.path.exists(path) or not _build.up_to_date():
         if not build_if_missing:
             raise RuntimeError(f"{path} is missing: run paper_1605_01800_gb300.build.build()")
         _build.build()
