@@ -11,6 +11,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbm.h"
 #include "lbm_launch.h"
@@ -21,6 +22,13 @@ using namespace lbm;
 namespace {
 
 thread_local std::string g_last_error;
+
+// NVTX range over one API call (shows up in Nsight Systems / Compute
+// timelines; free when no tool is attached)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -854,6 +862,7 @@ int lbm_set_stream(lbm_ctx* c, void* stream) {
 }
 
 int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy) {
+    Range range("lbm_init_fields");
     int rc = check_lat(c, lat);
     if (rc) return rc;
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
@@ -864,6 +873,7 @@ int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, co
 }
 
 int lbm_init_fields_all(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
+    Range range("lbm_init_fields_all");
     if (!c) return fail(LBM_EINVAL, "null context");
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
     int rc = init_range(c, 0, c->n, rho, ux, uy);
@@ -873,6 +883,7 @@ int lbm_init_fields_all(lbm_ctx* c, const double* rho, const double* ux, const d
 }
 
 int lbm_step(lbm_ctx* c, int n) {
+    Range range("lbm_step");
     if (!c) return fail(LBM_EINVAL, "null context");
     if (n < 0) return fail(LBM_EINVAL, "n=%d must be >= 0", n);
     int done = 0;
@@ -897,6 +908,7 @@ int lbm_step(lbm_ctx* c, int n) {
 }
 
 int lbm_read_moments(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, double* p) {
+    Range range("lbm_read_moments");
     int rc = check_lat(c, lat);
     if (rc) return rc;
     rc = moments_range(c, lat, 1, rho, ux, uy, p);
@@ -908,6 +920,7 @@ int lbm_read_moments(lbm_ctx* c, int lat, double* rho, double* ux, double* uy, d
 }
 
 int lbm_read_moments_all(lbm_ctx* c, double* rho, double* ux, double* uy, double* p) {
+    Range range("lbm_read_moments_all");
     if (!c) return fail(LBM_EINVAL, "null context");
     int rc = moments_range(c, 0, c->n, rho, ux, uy, p);
     if (rc) return rc;
@@ -920,6 +933,7 @@ int lbm_read_moments_all(lbm_ctx* c, double* rho, double* ux, double* uy, double
 }
 
 int lbm_total_mass(lbm_ctx* c, int lat, double* mass) {
+    Range range("lbm_total_mass");
     int rc = check_lat(c, lat);
     if (rc) return rc;
     if (!mass) return fail(LBM_EINVAL, "mass must not be null");
@@ -1002,6 +1016,7 @@ int copy_compact(lbm_ctx* c, char* host, bool to_host) {
 }  // namespace
 
 int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
+    Range range("lbm_save_state");
     size_t need = 0;
     int rc = lbm_state_size(c, &need);
     if (rc) return rc;
@@ -1024,6 +1039,7 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
 }
 
 int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
+    Range range("lbm_load_state");
     size_t need = 0;
     int rc = lbm_state_size(c, &need);
     if (rc) return rc;
@@ -1097,6 +1113,7 @@ int lbm_set_tile(lbm_ctx* c, int index) {
 }
 
 int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
+    Range range("lbm_autotune");
     if (!c) return fail(LBM_EINVAL, "null context");
     if (steps < 1) return fail(LBM_EINVAL, "steps=%d must be >= 1", steps);
     const size_t fbytes = (size_t)c->total_elems * c->elem;
