@@ -503,3 +503,29 @@ def test_injected_allocation_failures_leave_nothing_broken(monkeypatch):
     (again,) = run_gpu(specs[:1], "fp32_dev", 3)
     for x, y in zip(again, ref[0]):
         assert np.array_equal(x, y)
+
+
+def test_autotune_cache_measures_once_and_reuses(tmp_path):
+    """The first best_tile call for a kind of batch times every shape and
+    records the winner; a second context of the same kind reuses it without
+    timing, and the results stay those of any other shape."""
+    from paper_1605_01800_gb300 import autotune
+    specs = [small_spec(96, 64, seed=71), small_spec(64, 40, walls=True, seed=72)]
+    cache = str(tmp_path / "tiles.json")
+    b1 = lbm.Batch(specs, "fp32_dev")
+    b1.init()
+    r1 = autotune.best_tile(b1, steps=3, cache_path=cache)
+    assert not r1["cached"] and r1["ms"] is not None
+    b1.step(4)
+    got = [b1.moments(i) for i in range(2)]
+    b1.close()
+    b2 = lbm.Batch(specs, "fp32_dev")
+    before = b2.info()["kernel_launches"]
+    r2 = autotune.best_tile(b2, steps=3, cache_path=cache)
+    assert r2["cached"] and r2["tile"] == r1["tile"]
+    assert b2.info()["kernel_launches"] == before
+    b2.close()
+    ref = run_gpu(specs, "fp32_dev", 4, tile=0)
+    for a, b in zip(got, ref):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
