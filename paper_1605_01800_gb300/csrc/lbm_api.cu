@@ -89,14 +89,17 @@ struct lbm_ctx {
     Phys<float>* d_phys_f = nullptr;
     Phys<double>* d_phys_d = nullptr;
     Tile* d_tiles = nullptr;
-    int n_tiles = 0;             // tiles of the plain (or TMA) kernel
-    // pipelined variants: the full wall-free tiles go to the persistent
-    // kernel (d_fast, n_fast, pipe_grid CTAs), the rest (d_tiles) to the plain
-    // kernel of the same node tile
+    int n_tiles = 0;             // tiles of the plain kernel
+    // pipelined variants: the full wall-free tiles away from the lattice edges
+    // go to the persistent kernel (d_fast, n_fast, pipe_grid CTAs), the rest
+    // (d_tiles) to the plain kernel of the same node tile; TMA variants
+    // likewise take the tiles away from the edges (d_tma, n_tma)
     TileGeom* d_tgeo = nullptr;  // d_tiles with their lattices' geometry (plain kernel)
     FastTile* d_fast = nullptr;
     int n_fast = 0;
     int pipe_grid = 0;
+    Tile* d_tma = nullptr;
+    int n_tma = 0;
     // TMA variants: tensor maps per variant (box shape) and source buffer,
     // encoded once and passed to every launch as kernel parameters.
     static constexpr int kMaxTma = 8;
@@ -115,12 +118,11 @@ struct lbm_ctx {
     // can check the error path and the clean-up without exhausting a GPU
     long long fail_alloc_at = 0, alloc_count = 0;
     int tile_index = 0;
-    bool has_tiny = false;       // a lattice under 4 cells in x or y (see launch_one_step)
     unsigned* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_scalar = nullptr;
     double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
-    double* d_psi = nullptr;     // read-out scratch: one ghosted FP64 plane per lattice
+    double* d_psi = nullptr;     // read-out scratch: one FP64 psi plane per lattice
     unsigned* d_bad = nullptr;   // per-lattice invalid-input flags of the init kernel
     unsigned* h_bad = nullptr;   // their page-locked host copy
     std::vector<Phys<double>> phys_d;
@@ -256,6 +258,7 @@ void free_ctx(lbm_ctx* c) {
     for (int v = 0; v < lbm_ctx::kMaxTma; ++v)
         for (int b = 0; b < 2; ++b) delete c->h_maps[v][b];
     cudaFree(c->d_fast);
+    cudaFree(c->d_tma);
     cudaFree(c->d_tgeo);
     cudaFree(c->d_status);
     cudaFree(c->d_partials);
@@ -285,12 +288,9 @@ void tile_shape(int index, int* tx, int* ty) {
 
 // kernel launches of one step with the current tile list
 int launches_per_step(const lbm_ctx* c) {
-    int n = c->has_tiny ? 1 : 0;
-    if (is_pipe(c->tile_index))
-        n += (c->n_fast > 0 ? 1 : 0) + (c->n_tiles > 0 ? 1 : 0);
-    else
-        n += 1;
-    return n;
+    if (is_pipe(c->tile_index)) return (c->n_fast > 0 ? 1 : 0) + (c->n_tiles > 0 ? 1 : 0);
+    if (is_tma(c->tile_index)) return (c->n_tma > 0 ? 1 : 0) + (c->n_tiles > 0 ? 1 : 0);
+    return 1;
 }
 
 // Tensor maps for a TMA variant's box shape (built once per context and
@@ -327,22 +327,25 @@ int build_tma(lbm_ctx* c, int tile_index) {
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int per_sm = tma_blocks_per_sm(v);
     if (per_sm < 1) return fail(LBM_ECUDA, "TMA step variant %d cannot be resident on this device", tile_index);
-    c->tma_grid[v] = std::min(c->n_tiles, per_sm * sms);
+    c->tma_grid[v] = std::min(c->n_tma, per_sm * sms);
     return LBM_OK;
 }
 
-// Work-list of one step launch: every tile of every lattice, lattices in
-// creation order, tiles row-major within a lattice.
+// Work-lists of one step: every tile of every lattice, lattices in creation
+// order, tiles row-major within a lattice. The pipelined and TMA variants
+// take the tiles at least two cells away from every edge of their lattice
+// (the pipelined ones only wall-free Carnahan-Starling tiles); the plain
+// kernel of the same node tile takes the rest.
 int build_tiles(lbm_ctx* c, int tile_index) {
     if (tile_index < 0 || tile_index >= total_tiles()) return fail(LBM_EINVAL, "no tile shape %d", tile_index);
     if (tile_index >= kTileCount && c->precision == LBM_FP64)
         return fail(LBM_EINVAL, "tile %d is an FP32-only variant; this context stores FP64", tile_index);
     if (is_tma(tile_index) && c->n > kTmaMaxLattices)  // refused before the current tile list is replaced
         return fail(LBM_EINVAL, "tile %d (TMA) takes batches of at most %d lattices", tile_index, kTmaMaxLattices);
-    const bool pipe = is_pipe(tile_index);
+    const bool pipe = is_pipe(tile_index), tma = is_tma(tile_index);
     int tx = 0, ty = 0;
     tile_shape(tile_index, &tx, &ty);
-    std::vector<Tile> tiles;
+    std::vector<Tile> tiles, inner_tiles;
     std::vector<FastTile> fast;
     for (int l = 0; l < c->n; ++l) {
         const HostLattice& L = c->lats[l];
@@ -372,17 +375,17 @@ int build_tiles(lbm_ctx* c, int tile_index) {
                                   sat[(size_t)j1 * (ex + 1) + i0] + sat[(size_t)j0 * (ex + 1) + i0];
                     clear = n == 0;
                 }
-                // the pipelined kernel takes full tiles clear of walls in Carnahan-Starling
-                // lattices of at least 4 x 4
-                if (pipe && clear && full && g.nx >= 4 && g.ny >= 4 && L.desc.eos.kind == LBM_EOS_CS) {
-                    const int edge = x0 < 2 || x0 + tx > g.nx - 2 || y0 < 2 || y0 + ty > g.ny - 2;
-                    fast.push_back(FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, edge, {0, 0}});
-                } else {
+                // no pull of the tile or of its halo ring crosses an edge
+                const bool inner = x0 >= 2 && x0 + tx <= g.nx - 2 && y0 >= 2 && y0 + ty <= g.ny - 2;
+                if (pipe && clear && inner && L.desc.eos.kind == LBM_EOS_CS)
+                    fast.push_back(FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, {0, 0, 0}});
+                else if (tma && inner)
+                    inner_tiles.push_back(Tile{l, x0, y0, clear ? 1 : 0});
+                else
                     tiles.push_back(Tile{l, x0, y0, clear ? 1 : 0});
-                }
             }
     }
-    if (tiles.size() > (size_t)0x7fffffff || fast.size() > (size_t)0x7fffffff)
+    if (tiles.size() > (size_t)0x7fffffff || fast.size() > (size_t)0x7fffffff || inner_tiles.size() > (size_t)0x7fffffff)
         return fail(LBM_EINVAL, "too many tiles");
     std::vector<TileGeom> tgeo(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) tgeo[k] = TileGeom{c->lats[tiles[k].lat].geom, tiles[k]};
@@ -393,6 +396,8 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     if (!tiles.empty()) rc = dev_alloc(c, &d, tiles.size() * sizeof(Tile));
     if (!rc && !tiles.empty()) rc = dev_alloc(c, &dg, tgeo.size() * sizeof(TileGeom));
     if (!rc && !fast.empty()) rc = dev_alloc(c, &df, fast.size() * sizeof(FastTile));
+    Tile* di = nullptr;
+    if (!rc && !inner_tiles.empty()) rc = dev_alloc(c, &di, inner_tiles.size() * sizeof(Tile));
     if (rc) {
         if (d) {
             cudaFree(d);
@@ -402,12 +407,18 @@ int build_tiles(lbm_ctx* c, int tile_index) {
             cudaFree(dg);
             c->device_bytes -= tgeo.size() * sizeof(TileGeom);
         }
+        if (df) {
+            cudaFree(df);
+            c->device_bytes -= fast.size() * sizeof(FastTile);
+        }
         return rc;
     }
     cudaError_t e = cudaSuccess;
     if (d) e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && dg) e = cudaMemcpy(dg, tgeo.data(), tgeo.size() * sizeof(TileGeom), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && df) e = cudaMemcpy(df, fast.data(), fast.size() * sizeof(FastTile), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && di)
+        e = cudaMemcpy(di, inner_tiles.data(), inner_tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
     int per_sm = 0, sms = 0, dev = 0;
     if (e == cudaSuccess && pipe) {
         e = cudaGetDevice(&dev);
@@ -418,7 +429,9 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         cudaFree(d);
         cudaFree(dg);
         cudaFree(df);
-        c->device_bytes -= tiles.size() * (sizeof(Tile) + sizeof(TileGeom)) + fast.size() * sizeof(FastTile);
+        cudaFree(di);
+        c->device_bytes -= tiles.size() * (sizeof(Tile) + sizeof(TileGeom)) + fast.size() * sizeof(FastTile) +
+                           inner_tiles.size() * sizeof(Tile);
         return e != cudaSuccess ? cuda_fail(e, "tile list upload")
                                 : fail(LBM_ECUDA, "pipelined variant %d cannot be resident on this device", tile_index);
     }
@@ -434,12 +447,18 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         cudaFree(c->d_fast);
         c->device_bytes -= (size_t)c->n_fast * sizeof(FastTile);
     }
+    if (c->d_tma) {
+        cudaFree(c->d_tma);
+        c->device_bytes -= (size_t)c->n_tma * sizeof(Tile);
+    }
     c->d_tiles = d;
     c->d_tgeo = dg;
     c->n_tiles = (int)tiles.size();
     c->d_fast = df;
     c->n_fast = (int)fast.size();
     c->pipe_grid = pipe ? (int)std::min<long long>(c->n_fast, (long long)per_sm * sms) : 0;
+    c->d_tma = di;
+    c->n_tma = (int)inner_tiles.size();
     c->tile_index = tile_index;
     drop_graphs(c);
     if (is_tma(tile_index)) return build_tma(c, tile_index);
@@ -491,19 +510,20 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         }
     } else if (c->tile_index >= kTileCount) {
         const int v = c->tile_index - kTileCount;
-        TmaArgs a{c->d_tiles, c->n_tiles, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status,
-                  c->tma_wait_limit, c->tma_extra_tx};
-        e = launch_step_tma(v, c->tma_grid[v], a, *c->h_maps[v][src], *c->h_table, c->stream);
+        TmaArgs ta{c->d_tma, c->n_tma, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status,
+                   c->tma_wait_limit, c->tma_extra_tx};
+        e = launch_step_tma(v, c->tma_grid[v], ta, *c->h_maps[v][src], *c->h_table, c->stream);
+        if (e == cudaSuccess && c->n_tiles > 0) {
+            StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
+                              (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
+            e = launch_step_f32(tma_plain_partner(v), c->n_tiles, a, c->h_table, c->stream);
+        }
     } else {
         StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
                           (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
         e = launch_step_f32(c->tile_index, c->n_tiles, a, c->h_table, c->stream);
     }
-    if (e != cudaSuccess || !c->has_tiny) return e;
-    // lattices under 4 cells wide or high: rewrite their ghost frames
-    const LaunchSet ls = launch_set(c, 0, c->n);
-    return c->precision == LBM_FP64 ? launch_ghost_refresh_f64(ls, (double*)c->f[1 - src], c->stream)
-                                    : launch_ghost_refresh_f32(ls, (float*)c->f[1 - src], c->stream);
+    return e;
 }
 
 bool capturable_stream(cudaStream_t s) {
@@ -637,12 +657,6 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
         e = launch_init_f32(ls, k_rho, k_ux, k_uy, (float*)c->f[c->cur], c->d_bad, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     c->launches += 1;
-    if (c->has_tiny) {  // lattices under 4 cells: their ghost frames are written separately
-        e = c->precision == LBM_FP64 ? launch_ghost_refresh_f64(ls, (double*)c->f[c->cur], c->stream)
-                                     : launch_ghost_refresh_f32(ls, (float*)c->f[c->cur], c->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "ghost refresh kernel");
-        c->launches += 1;
-    }
     // the host arrays may be pageable and the staging buffer is reused: wait,
     // then report invalid input found by the init kernel
     CK(cudaMemcpyAsync(c->h_bad, c->d_bad, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
@@ -747,7 +761,6 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
         L.c_off = c->compact_elems;
         c->compact_elems += round_up(9 * (long long)g.ny * round_up(g.nx, 32), 64);
         node_off += nn;
-        if (g.nx < 4 || g.ny < 4) c->has_tiny = true;
         c->total_nodes += nn;
         c->fluid_nodes += L.n_fluid;
         c->max_nodes = std::max(c->max_nodes, nn);
@@ -796,7 +809,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
             const HostLattice& L = c->lats[i];
             if (L.mask.empty()) continue;
             const Geom& g = L.geom;
-            // nodes and their periodic images in the ghost frame
+            // the nodes, and their periodic images in the frame (no pull reads them)
             rows.assign((size_t)g.plane, 0);
             for (int y = -kGY; y < g.ny + kGY; ++y)
                 for (int x = -2; x < g.nx + 2; ++x) {
@@ -991,7 +1004,7 @@ int lbm_state_size(lbm_ctx* c, size_t* bytes) {
 
 namespace {
 
-// Copy every lattice's nodes between the device layout (ghost frame, row
+// Copy every lattice's nodes between the device layout (frame, row
 // pitch `pitch`) and the compact checkpoint layout (plane a of lattice l at
 // c_off + a*ny*cpitch, node (x, y) at y*cpitch + x, cpitch = round_up(nx, 32)).
 int copy_compact(lbm_ctx* c, char* host, bool to_host) {
@@ -1064,11 +1077,6 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     drop_graphs(c);
     rc = copy_compact(c, const_cast<char*>(p), false);
     if (rc) return rc;
-    const LaunchSet ls = launch_set(c, 0, c->n);
-    cudaError_t e = c->precision == LBM_FP64 ? launch_ghost_refresh_f64(ls, (double*)c->f[c->cur], c->stream)
-                                             : launch_ghost_refresh_f32(ls, (float*)c->f[c->cur], c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ghost refresh kernel");
-    c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));
     c->steps = steps;
     return LBM_OK;
@@ -1211,7 +1219,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->kernel_launches = c->launches;
     info->device_bytes = c->device_bytes;
     tile_shape(c->tile_index, &info->tile_x, &info->tile_y);
-    info->n_tiles = c->n_tiles + c->n_fast;
+    info->n_tiles = c->n_tiles + c->n_fast + c->n_tma;
     info->graph_chunk = kGraphChunk;
     return LBM_OK;
 }

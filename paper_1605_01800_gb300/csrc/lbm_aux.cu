@@ -81,7 +81,7 @@ template <typename T>
 __device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask, int x, int y,
                                             double out[9]) {
     T tmp[9];
-    if (pull_node<T>(f, mask, (int)g.plane, g.pitch, node_index(g, x, y), tmp)) return false;
+    if (pull_node<T>(f, mask, (int)g.plane, nbr_of(g.nx, g.ny, g.pitch, x, y), tmp)) return false;
     for (int a = 0; a < 9; ++a) out[a] = (double)tmp[a];
     return true;
 }
@@ -92,10 +92,10 @@ __device__ __forceinline__ double psi_fp64(double rho, const Phys<double>& P) {
 }
 
 // Read-out, pass 1: for every cell with x in [-1, nx], y in [-1, ny] (the
-// nodes and the ghost cells next to them) the pulled distribution gives rho
-// and psi (Eq. 13) in FP64; psi goes to a plane in the ghosted layout
-// (-1 at solid cells), rho and the momentum sum_a e_a f_a of the nodes to
-// the output arrays.
+// nodes and, in the frame, their periodic neighbours across each edge) the
+// pulled distribution gives rho and psi (Eq. 13) in FP64; psi goes to a
+// plane in the stored layout (-1 at solid cells), rho and the momentum
+// sum_a e_a f_a of the nodes to the output arrays.
 template <typename T>
 __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                                    int lat0, const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
@@ -237,25 +237,6 @@ __global__ void mass_final_kernel(const double* __restrict__ partials, double rh
     *out = s + rho_ref * (double)n_fluid;
 }
 
-// Rewrite every lattice's ghost frame from the nodes it images (after the
-// node values were written by a copy, e.g. when a checkpoint is loaded).
-template <typename T>
-__global__ void ghost_refresh_kernel(const Geom* __restrict__ geoms, int lat0, T* __restrict__ f_base) {
-    const int lat = lat0 + blockIdx.y;
-    const Geom g = geoms[lat];
-    T* f = f_base + g.f_off;
-    const long long n = (long long)g.nx * g.ny;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx), y = (int)(i / g.nx);
-        if (!(x < 2 || x >= g.nx - 2 || y < 2 || y >= g.ny - 2)) continue;
-        T v[9];
-        const int c = node_index(g, x, y);
-        for (int a = 0; a < 9; ++a) v[a] = f[a * g.plane + c];
-        store_ghost_images<T>(f, g, x, y, v);
-    }
-}
-
 dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
     long long bx = (max_nodes + threads - 1) / threads;
     if (bx > 4096) bx = 4096;
@@ -301,20 +282,7 @@ cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T*
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t ghost_impl(const LaunchSet& L, T* f, cudaStream_t s) {
-    ghost_refresh_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(L.geoms, L.lat0, f);
-    return cudaGetLastError();
-}
-
 }  // namespace
-
-cudaError_t launch_ghost_refresh_f32(const LaunchSet& L, float* f, cudaStream_t s) {
-    return ghost_impl<float>(L, f, s);
-}
-cudaError_t launch_ghost_refresh_f64(const LaunchSet& L, double* f, cudaStream_t s) {
-    return ghost_impl<double>(L, f, s);
-}
 
 cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
                             const double* uy, float* f, unsigned* bad, cudaStream_t s) {

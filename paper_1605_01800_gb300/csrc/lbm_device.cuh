@@ -4,14 +4,15 @@
 // Layout in HBM (one array per ping-pong buffer, all lattices of a batch):
 //   lattice L owns 9 planes starting at element geom[L].f_off; plane a holds
 //   f_a (or its deviation f_a - w_a rho_ref) at element a*plane + idx(x, y),
-//   idx(x, y) = (y + kGY) * pitch + x + kGX. Around the nx x ny nodes each
-//   plane keeps a two-cell ghost frame (x in {-2, -1, nx, nx + 1}, y in
-//   {-2, -1, ny, ny + 1}) holding the periodic images of the edge nodes; the
-//   kernel that writes a node also writes its images. Streaming therefore
-//   needs no wrap-around arithmetic, and any tile plus a two-cell halo is a
-//   plain rectangle of memory. kGX = 32 keeps node x = 0 (and every row's
-//   first node) on a 128-byte boundary; pitch = round_up(nx + 34, 32).
-//   The wall mask uses the same idx() (one byte per cell, ghosts included).
+//   idx(x, y) = (y + kGY) * pitch + x + kGX. kGX = 32 keeps node x = 0 (and
+//   every row's first node) on a 128-byte boundary; pitch = round_up(nx + 34,
+//   32). The frame around the nodes (kGY rows above and below, the columns
+//   left and right of them) holds no populations: periodic streaming wraps
+//   by address arithmetic (Nbr below), so a step reads and writes only the
+//   nodes themselves, 9 + 9 populations each, with no copies of edge nodes
+//   to keep in step. The frame gives the read-out's psi plane room for its
+//   one-cell halo. The wall mask uses the same idx() (one byte per cell; its
+//   frame holds the periodic images, written once by the host).
 //
 // Velocity numbering (weights of Eq. 7: axis 1-4, diagonal 5-8):
 //   e0 (0,0) e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1)
@@ -85,12 +86,25 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Wrap an index that is at most one period outside [0, n) without a division;
-// only lattices narrower than the tile need the general wrap_index.
-__device__ __forceinline__ int wrap_near(int i, int n) {
-    i = (i < 0) ? i + n : i;
-    i = (i >= n) ? i - n : i;
-    return (i >= 0 && i < n) ? i : wrap_index(i, n);
+// Stored index of node (x, y) and the offsets from it to its four axis
+// neighbours on the periodic lattice (Eq. 5 with periodic boundaries): the
+// neighbour across an edge is the node at the far side of the same row or
+// column. x in [-1, nx] and y in [-1, ny] (one period outside at most) are
+// first brought into the lattice, so a halo cell beside an edge is the node
+// it stands for. Valid for any nx, ny >= 1.
+struct Nbr {
+    int c, xm, xp, ym, yp;
+};
+__device__ __forceinline__ Nbr nbr_of(int nx, int ny, int pitch, int x, int y) {
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    Nbr n;
+    n.c = (y + kGY) * pitch + x + kGX;
+    n.xm = x == 0 ? nx - 1 : -1;
+    n.xp = x == nx - 1 ? 1 - nx : 1;
+    n.ym = y == 0 ? (ny - 1) * pitch : -pitch;
+    n.yp = y == ny - 1 ? (1 - ny) * pitch : pitch;
+    return n;
 }
 
 // psi of Eq. 13 with the CS pressure of Eq. 15, written as
@@ -172,31 +186,49 @@ __device__ __forceinline__ uint8_t ld_mask(const uint8_t* __restrict__ m, int i,
     return m[i];
 }
 
-// Gather the distribution of the cell at stored index c after streaming
-// (Eq. 5) from the post-collision array `fin` (pull form):
-// f_a(x) = f*_a(x - e_a); periodic images come from the ghost frame, so c may
-// be any cell with x in [-1, nx] and y in [-1, ny]. With a wall mask, a link
-// whose source is solid is reflected: f_a(x) = f*_abar(x). Returns true if
-// the cell itself is solid (then f is not filled).
+// Gather the distribution of node n after streaming (Eq. 5) from the
+// post-collision array `fin` (pull form): f_a(x) = f*_a(x - e_a), with x - e_a
+// taken periodically. With a wall mask, a link whose source is solid is
+// reflected: f_a(x) = f*_abar(x). Returns true if the node itself is solid
+// (then f is not filled).
 template <typename T>
 __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8_t* __restrict__ mask,
-                                          int plane, int pitch, int c, T f[9]) {
+                                          int plane, const Nbr& n, T f[9]) {
     const int np = 9 * plane;  // < 2^31 (checked when the lattice is created)
     auto F = [&](int a, int i) { return ld_pop<T>(fin, a * plane + i, np); };
+    const int c = n.c;
     if (mask != nullptr) {
         auto M = [&](int i) { return ld_mask(mask, i, plane); };
         if (M(c)) return true;
         f[0] = F(0, c);
-        f[1] = M(c - 1)         ? F(3, c) : F(1, c - 1);
-        f[2] = M(c - pitch)     ? F(4, c) : F(2, c - pitch);
-        f[3] = M(c + 1)         ? F(1, c) : F(3, c + 1);
-        f[4] = M(c + pitch)     ? F(2, c) : F(4, c + pitch);
-        f[5] = M(c - pitch - 1) ? F(7, c) : F(5, c - pitch - 1);
-        f[6] = M(c - pitch + 1) ? F(8, c) : F(6, c - pitch + 1);
-        f[7] = M(c + pitch + 1) ? F(5, c) : F(7, c + pitch + 1);
-        f[8] = M(c + pitch - 1) ? F(6, c) : F(8, c + pitch - 1);
+        f[1] = M(c + n.xm)        ? F(3, c) : F(1, c + n.xm);
+        f[2] = M(c + n.ym)        ? F(4, c) : F(2, c + n.ym);
+        f[3] = M(c + n.xp)        ? F(1, c) : F(3, c + n.xp);
+        f[4] = M(c + n.yp)        ? F(2, c) : F(4, c + n.yp);
+        f[5] = M(c + n.ym + n.xm) ? F(7, c) : F(5, c + n.ym + n.xm);
+        f[6] = M(c + n.ym + n.xp) ? F(8, c) : F(6, c + n.ym + n.xp);
+        f[7] = M(c + n.yp + n.xp) ? F(5, c) : F(7, c + n.yp + n.xp);
+        f[8] = M(c + n.yp + n.xm) ? F(6, c) : F(8, c + n.yp + n.xm);
         return false;
     }
+    f[0] = F(0, c);
+    f[1] = F(1, c + n.xm);
+    f[2] = F(2, c + n.ym);
+    f[3] = F(3, c + n.xp);
+    f[4] = F(4, c + n.yp);
+    f[5] = F(5, c + n.ym + n.xm);
+    f[6] = F(6, c + n.ym + n.xp);
+    f[7] = F(7, c + n.yp + n.xp);
+    f[8] = F(8, c + n.yp + n.xm);
+    return false;
+}
+
+// pull_node for a node at stored index c whose eight neighbours all lie
+// inside the lattice (no wrap) and are fluid: fixed offsets only.
+template <typename T>
+__device__ __forceinline__ void pull_inner(const T* __restrict__ fin, int plane, int pitch, int c, T f[9]) {
+    const int np = 9 * plane;
+    auto F = [&](int a, int i) { return ld_pop<T>(fin, a * plane + i, np); };
     f[0] = F(0, c);
     f[1] = F(1, c - 1);
     f[2] = F(2, c - pitch);
@@ -206,60 +238,10 @@ __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8
     f[6] = F(6, c - pitch + 1);
     f[7] = F(7, c + pitch + 1);
     f[8] = F(8, c + pitch - 1);
-    return false;
 }
 
-// Write the nine values of node (x, y) (0 <= x < nx, 0 <= y < ny) and, for a
-// node within two cells of an edge, every ghost cell whose periodic image it
-// is. `base` is plane 0 of the lattice.
-template <typename T>
-__device__ __forceinline__ void store_ghost_images(T* __restrict__ base, const Geom& g, int x, int y,
-                                                const T v[9]) {
-    int xs[5], ys[5];
-    int nxs = 0, nys = 0;
-    xs[nxs++] = x;
-    ys[nys++] = y;
-    const int gxs[4] = {-2, -1, g.nx, g.nx + 1};
-    const int gys[4] = {-2, -1, g.ny, g.ny + 1};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (wrap_index(gxs[k], g.nx) == x) xs[nxs++] = gxs[k];
-        if (wrap_index(gys[k], g.ny) == y) ys[nys++] = gys[k];
-    }
-    for (int j = 0; j < nys; ++j)
-        for (int i = 0; i < nxs; ++i) {
-            if (i == 0 && j == 0) continue;
-            const int c = node_index(g, xs[i], ys[j]);
-            for (int a = 0; a < 9; ++a) st_pop<T>(base, (int)(a * g.plane + c), (int)(9 * g.plane), v[a]);
-        }
-}
-
-// The ghost images of node (x, y) at stored index c: for a node within two
-// cells of an edge of a lattice at least 4 x 4, each of x +- nx, y +- ny and
-// the corner combination gets a copy of v (one image per direction at most).
-template <typename T>
-__device__ __forceinline__ void store_images(T* __restrict__ base, const Geom& g, int c, int x, int y,
-                                             const T v[9]) {
-    const bool ex = x < 2 || x >= g.nx - 2;
-    const bool ey = y < 2 || y >= g.ny - 2;
-    if (!(ex || ey)) return;
-    const int plane = (int)g.plane;
-    const int dx = !ex ? 0 : (x < 2 ? g.nx : -g.nx);
-    const int dy = !ey ? 0 : (y < 2 ? g.ny : -g.ny) * g.pitch;
-    if (dx != 0) {
-#pragma unroll
-        for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c + dx, 9 * plane, v[a]);
-    }
-    if (dy != 0) {
-#pragma unroll
-        for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c + dy, 9 * plane, v[a]);
-        if (dx != 0) {
-#pragma unroll
-            for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c + dx + dy, 9 * plane, v[a]);
-        }
-    }
-}
-
+// Write the nine values of node (x, y), 0 <= x < nx, 0 <= y < ny; `base` is
+// plane 0 of the lattice.
 template <typename T>
 __device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, int x, int y,
                                            const T v[9]) {
@@ -267,10 +249,6 @@ __device__ __forceinline__ void store_node(T* __restrict__ base, const Geom& g, 
     const int plane = (int)g.plane;
 #pragma unroll
     for (int a = 0; a < 9; ++a) st_pop<T>(base, a * plane + c, 9 * plane, v[a]);
-    // lattices under 4 cells in x or y can have several images per node;
-    // their frames are rewritten by ghost_refresh_kernel after each step
-    if (g.nx < 4 || g.ny < 4) return;
-    store_images<T>(base, g, c, x, y, v);
 }
 
 // Sum of the eight moving populations in a fixed association; the density

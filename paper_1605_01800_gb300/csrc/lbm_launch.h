@@ -26,6 +26,10 @@ struct PhysTable;
 
 // TMA-staged persistent FP32 variants (lbm_step_tma.cu); tile indices
 // kTileCount .. kTileCount + tma_variant_count() - 1 of the public tile list.
+// They take the tiles at least two cells away from every lattice edge (their
+// boxes are plain rectangles of the lattice); the other tiles of the step go
+// through the plain kernel of the same node tile (tma_plain_partner) in a
+// second launch.
 struct TmaArgs {
     const Tile* tiles;
     int n_tiles;
@@ -45,6 +49,7 @@ struct TmaMaps {
 };
 int tma_variant_count();
 void tma_variant_shape(int v, int* tx, int* ty);
+int tma_plain_partner(int v);
 int tma_blocks_per_sm(int v);
 cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps,
                             const PhysTable<float>& table, cudaStream_t s);
@@ -55,13 +60,14 @@ bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const
 
 // Persistent software-pipelined FP32 variants (lbm_step_pipe.cu); tile
 // indices kTileCount + tma_variant_count() + v. They take the full wall-free
-// tiles (FastTile list); the other tiles of the step go through the plain
+// tiles at least two cells away from every lattice edge (FastTile list:
+// fixed-offset pulls only); the other tiles of the step go through the plain
 // kernel of the same node tile (pipe_plain_partner) in a second launch.
 struct FastTile {
     long long f_off;       // plane 0 of the tile's lattice (element offset, both buffers)
     int plane, pitch, nx, ny;
-    int lat, x0, y0, edge; // edge: within two cells of a lattice edge (writes ghost images)
-    int pad[2];
+    int lat, x0, y0;
+    int pad[3];
 };
 struct PipeArgs {
     const FastTile* fast;
@@ -103,7 +109,8 @@ cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double*
 
 // rho, v (Eq. 6), p (Eq. 10) into device arrays indexed like the init inputs
 // (all four required), computed in FP64 from the stored distribution; psi is
-// scratch of one ghosted plane per lattice (element offset f_off / 9).
+// scratch of one plane per lattice in the stored layout (element offset
+// f_off / 9), its frame holding the psi of the periodic neighbours.
 cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s);
 cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* ux,
@@ -112,10 +119,6 @@ cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* psi,
 // rho alone (the first output of launch_moments_*, same values).
 cudaError_t launch_density_f32(const LaunchSet& L, const float* f, double* rho, cudaStream_t s);
 cudaError_t launch_density_f64(const LaunchSet& L, const double* f, double* rho, cudaStream_t s);
-
-// Rewrite the ghost frames of lattices [lat0, lat0 + n_lat) from their nodes.
-cudaError_t launch_ghost_refresh_f32(const LaunchSet& L, float* f, cudaStream_t s);
-cudaError_t launch_ghost_refresh_f64(const LaunchSet& L, double* f, cudaStream_t s);
 
 // Fixed-order FP64 mass of one lattice: sum over fluid nodes of the stored
 // values plus rho_ref * n_fluid. `partials` is scratch of kMassBlocks doubles.

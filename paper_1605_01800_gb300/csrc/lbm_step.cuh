@@ -8,10 +8,10 @@
 // (pulling the nine populations of each halo node, which neighbouring CTAs
 // also read, so those reads hit L2) and keeps it in shared memory. Each
 // thread's own nodes keep their nine pulled populations in registers between
-// the psi phase and the collision, so DRAM sees 9 reads + 9 writes per node
-// (plus the ghost images of edge nodes). The ghost frame of the layout makes
-// every pull a fixed offset. All RY * 9 loads of a thread are issued before
-// any of them is used.
+// the psi phase and the collision, so DRAM sees 9 reads + 9 writes per node.
+// Pulls inside a lattice are fixed offsets; tiles at a lattice edge wrap the
+// pulls that cross it (nbr_of). All RY * 9 loads of a thread are issued
+// before any of them is used.
 #pragma once
 
 #include <type_traits>
@@ -196,12 +196,13 @@ __device__ __forceinline__ void f32_collide_store(float (&f)[RY][9], const bool 
 // 4 x 4 nodes with no solid cell in the tile or its two-cell frame (every
 // tile of a wall-free lattice). Every own node and halo cell is fluid, so there
 // are no liveness tests; a thread's nodes stay in register pairs (F2) from
-// the loads to the stores, and the ghost images are written only by tiles
-// within two cells of an edge. The arithmetic is that of the general path
+// the loads to the stores, and only tiles within two cells of a lattice edge
+// compute wrapped pull offsets. The arithmetic is that of the general path
 // operation for operation, so both give bitwise the same result.
 
 // the nine pulled populations of the vertically adjacent nodes at stored
-// indices c and c + pitch, as pairs (no walls)
+// indices c and c + pitch, as pairs (no walls, no wrap: every source node
+// lies inside the lattice)
 __device__ __forceinline__ void pull_pair(const float* __restrict__ fin, int plane, int pitch, int c, F2 f[9]) {
     const int np = 9 * plane;
     auto ld2 = [&](int i) { return F2{make_float2(ld_pop(fin, i, np), ld_pop(fin, i + pitch, np))}; };
@@ -216,15 +217,33 @@ __device__ __forceinline__ void pull_pair(const float* __restrict__ fin, int pla
     f[8] = ld2(8 * plane + c + pitch - 1);
 }
 
+// pull_pair for a pair at a lattice edge: the first node at stored index c
+// (column x, row y), the second one row below it (y + 1 < ny); dxm, dxp are
+// the offsets to columns x - 1 and x + 1, rm the offset from row y to row
+// y - 1 and rp2 the one from row y + 1 to row y + 2, each periodic (nbr_of).
+__device__ __forceinline__ void pull_pair_wrap(const float* __restrict__ fin, int plane, int pitch, int c,
+                                               int dxm, int dxp, int rm, int rp2, F2 f[9]) {
+    const int np = 9 * plane;
+    auto ld2 = [&](int i0, int i1) { return F2{make_float2(ld_pop(fin, i0, np), ld_pop(fin, i1, np))}; };
+    const int d = c + pitch;  // the second node
+    f[0] = ld2(c, d);
+    f[1] = ld2(plane + c + dxm, plane + d + dxm);
+    f[2] = ld2(2 * plane + c + rm, 2 * plane + c);
+    f[3] = ld2(3 * plane + c + dxp, 3 * plane + d + dxp);
+    f[4] = ld2(4 * plane + d, 4 * plane + d + rp2);
+    f[5] = ld2(5 * plane + c + rm + dxm, 5 * plane + c + dxm);
+    f[6] = ld2(6 * plane + c + rm + dxp, 6 * plane + c + dxp);
+    f[7] = ld2(7 * plane + d + dxp, 7 * plane + d + rp2 + dxp);
+    f[8] = ld2(8 * plane + d + dxm, 8 * plane + d + rp2 + dxm);
+}
+
 // Force (Eq. 7), collision (Eq. 3) and store of the node pair in tile-local
 // column lx, rows ly and ly + 1 (psi tile s_psi with a one-cell frame, row
-// stride SW), lattice column x, rows y and y + 1, stored index cs of the
-// first node; the ghost images too when the tile is near an edge.
+// stride SW), stored index cs of the first node.
 template <int SW>
 __device__ __forceinline__ void f32_pair_finish(F2 (&f)[9], F2 rho, F2 drho, F2 psi, const float* s_psi, int lx,
                                                 int ly, const Phys<float>& P, float* __restrict__ fo, int cs,
-                                                bool edge, const Geom& g, int x, int y) {
-    const int plane = (int)g.plane, pitch = g.pitch;
+                                                int plane, int pitch) {
     const int c = (ly + 1) * SW + lx + 1;
     auto nb2 = [&](int o) { return F2{make_float2(s_psi[c + o], s_psi[c + SW + o])}; };
     F2 gx, gy;
@@ -237,16 +256,6 @@ __device__ __forceinline__ void f32_pair_finish(F2 (&f)[9], F2 rho, F2 drho, F2 
     for (int a = 0; a < 9; ++a) {
         st_pop(fo, a * plane + cs, 9 * plane, f[a].v.x);
         st_pop(fo, a * plane + cs + pitch, 9 * plane, f[a].v.y);
-    }
-    if (edge) {
-        float v0[9], v1[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            v0[a] = f[a].v.x;
-            v1[a] = f[a].v.y;
-        }
-        store_images<float>(fo, g, cs, x, y, v0);
-        store_images<float>(fo, g, cs + pitch, x, y + 1, v1);
     }
 }
 
@@ -287,9 +296,24 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
     const int x = tile.x0 + lx, y0 = tile.y0 + ly0;
     const int c0 = node_index(g, x, y0);
 
+    // a tile within two cells of an edge has pulls (of its nodes or of its
+    // halo ring) that cross it; the others use fixed offsets only
+    const bool edge = tile.x0 < 2 || tile.x0 + TX > g.nx - 2 || tile.y0 < 2 || tile.y0 + TY > g.ny - 2;
     F2 f[NP][9];
+    if (edge) {
+        const int dxm = x == 0 ? g.nx - 1 : -1;
+        const int dxp = x == g.nx - 1 ? 1 - g.nx : 1;
 #pragma unroll
-    for (int p = 0; p < NP; ++p) pull_pair(fin, plane, pitch, c0 + 2 * p * pitch, f[p]);
+        for (int p = 0; p < NP; ++p) {
+            const int y = y0 + 2 * p;
+            const int rm = y == 0 ? (g.ny - 1) * pitch : -pitch;
+            const int rp2 = y + 1 == g.ny - 1 ? (1 - g.ny) * pitch : pitch;
+            pull_pair_wrap(fin, plane, pitch, c0 + 2 * p * pitch, dxm, dxp, rm, rp2, f[p]);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) pull_pair(fin, plane, pitch, c0 + 2 * p * pitch, f[p]);
+    }
 
     // halo ring: psi only
     float ph[NHT];
@@ -303,8 +327,12 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
             int cx, cy;
             halo_ring_cell<SW, SH>(h, cx, cy);
             hc[k] = cy * SW + cx;
+            const int hx = tile.x0 - 1 + cx, hy = tile.y0 - 1 + cy;
             float fh[9];
-            pull_node<float>(fin, nullptr, plane, pitch, node_index(g, tile.x0 - 1 + cx, tile.y0 - 1 + cy), fh);
+            if (edge)
+                pull_node<float>(fin, nullptr, plane, nbr_of(g.nx, g.ny, pitch, hx, hy), fh);
+            else
+                pull_inner<float>(fin, plane, pitch, node_index(g, hx, hy), fh);
             ph[k] = f32_halo_psi<false>(fh, rho_ref, P, flag);
         }
     }
@@ -326,11 +354,10 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
     if (flag) atomicOr(&A.status[tile.lat], flag);
 
     float* __restrict__ fo = A.fout + g.f_off;
-    const bool edge = tile.x0 < 2 || tile.x0 + TX > g.nx - 2 || tile.y0 < 2 || tile.y0 + TY > g.ny - 2;
 #pragma unroll
     for (int p = 0; p < NP; ++p)
-        f32_pair_finish<SW>(f[p], rho[p], drho[p], psi[p], s_psi, lx, ly0 + 2 * p, P, fo, c0 + 2 * p * pitch, edge,
-                            g, x, y0 + 2 * p);
+        f32_pair_finish<SW>(f[p], rho[p], drho[p], psi[p], s_psi, lx, ly0 + 2 * p, P, fo, c0 + 2 * p * pitch,
+                            plane, pitch);
 }
 
 // One tile by the general path (any tile: partial, walled, tiny lattices).
@@ -349,9 +376,10 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
     const T rho_ref = P.rho_ref;
     unsigned flag = 0;
 
-    // ---- own nodes: column x, rows y0 .. y0 + RY - 1. Cells past the last
-    // node (a tile overhanging the lattice) are pulled only up to x = nx and
-    // y = ny, the ghost images the last nodes' forces need.
+    // ---- own nodes: column x, rows y0 .. y0 + RY - 1. Of the cells past the
+    // last node (a tile overhanging the lattice) only x = nx and y = ny are
+    // pulled: they stand for nodes 0 (periodic), whose psi the last nodes'
+    // forces need.
     const int lx = threadIdx.x;
     const int x = tile.x0 + lx;
     const int y0 = tile.y0 + threadIdx.y * RY;
@@ -361,7 +389,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
     for (int r = 0; r < RY; ++r) {
         const int y = y0 + r;
         live[r] = (x <= nx) && (y <= ny);
-        if (live[r]) live[r] = !pull_node<T>(fin, mask, plane, pitch, node_index(g, x, y), f[r]);
+        if (live[r]) live[r] = !pull_node<T>(fin, mask, plane, nbr_of(nx, ny, pitch, x, y), f[r]);
     }
 
     // ---- halo ring: psi only (issued before the own nodes' arithmetic)
@@ -389,8 +417,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
             hc[k] = cy * SW + cx;
             const int hx = tile.x0 - 1 + cx, hy = tile.y0 - 1 + cy;
             T fh[9];
-            if (hx <= nx && hy <= ny &&
-                !pull_node<T>(fin, mask, plane, pitch, node_index(g, hx, hy), fh)) {
+            if (hx <= nx && hy <= ny && !pull_node<T>(fin, mask, plane, nbr_of(nx, ny, pitch, hx, hy), fh)) {
                 if constexpr (std::is_same<T, float>::value)
                     ph[k] = f32_halo_psi(fh, rho_ref, P, flag);
                 else
@@ -446,7 +473,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
             const T Fy = mG * psi[r] * gy;
             // ---- collision, Eq. 3
             collide<T>(f[r], rho[r], drho[r], Fx, Fy, G2 * (gx * gx + gy * gy), P);
-            // ---- store f* (and its ghost images near an edge)
+            // ---- store f*
             store_node<T>(fo, g, x, y, f[r]);
         }
     }

@@ -8,9 +8,10 @@
 // keeps two register sets: after the psi barrier of tile k it issues the
 // pulled loads of its next tile (own node pairs and its halo cell) and only
 // then does the force, the collision and the stores of tile k, so those loads
-// are in flight while it computes. Tiles that need the general path (partial
-// tiles, walls, lattices under 4 x 4) go through step_kernel in a second
-// launch of the same step; the two launches write disjoint nodes.
+// are in flight while it computes. Its tiles lie at least two cells from every
+// lattice edge, so every pull is a fixed offset. The other tiles (edge tiles,
+// partial tiles, walls, lattices under 4 x 4) go through step_kernel in a
+// second launch of the same step; the two launches write disjoint nodes.
 #include "lbm_launch.h"
 #include "lbm_step.cuh"
 
@@ -24,8 +25,7 @@ __device__ __forceinline__ void pipe_load(const float* __restrict__ fin, const F
     const float* __restrict__ base = fin + T.f_off;
     const int pitch = T.pitch, plane = T.plane;
     pull_pair(base, plane, pitch, (T.y0 + ly0 + kGY) * pitch + T.x0 + lx + kGX, f);
-    if (has_h)
-        pull_node<float>(base, nullptr, plane, pitch, (T.y0 - 1 + hcy + kGY) * pitch + T.x0 - 1 + hcx + kGX, fh);
+    if (has_h) pull_inner<float>(base, plane, pitch, (T.y0 - 1 + hcy + kGY) * pitch + T.x0 - 1 + hcx + kGX, fh);
 }
 
 template <int TX, int TYT, int MINB, bool TABLE>
@@ -86,10 +86,9 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
         float fhn[9];
         if (more) pipe_load(A.fin, Tn, lx, ly0, has_h, hcx, hcy, fn, fhn);
 
-        const Geom g{T.nx, T.ny, T.pitch, 0, T.f_off, T.plane, 0, 0};
         const int x = T.x0 + lx, y = T.y0 + ly0;
         f32_pair_finish<SW>(f, rho, drho, psi, s_psi, lx, ly0, P, A.fout + T.f_off,
-                            (y + kGY) * T.pitch + x + kGX, T.edge != 0, g, x, y);
+                            (y + kGY) * T.pitch + x + kGX, T.plane, T.pitch);
         __syncthreads();  // s_psi is rewritten by the next tile
         if (!more) break;
         t = tn;

@@ -7,8 +7,9 @@
 // it needs, per population a, the post-collision values of the tile plus a
 // two-cell frame: one 3-D TMA box load per population ({TX+8, TY+4, 1} at
 // stored (x0 + kGX - 4, y0 + kGY - 2, a); the x origin is 16-byte aligned) and,
-// for lattices with walls, one 2-D box of the wall mask. The ghost frame of
-// the layout makes every box a plain rectangle, also at the lattice edges.
+// for lattices with walls, one 2-D box of the wall mask. The kernel takes the
+// tiles at least two cells away from every lattice edge, so a box holds the
+// nodes it stands for and no pull wraps; the plain kernel does the others.
 // Loads for the next S - 1 tiles are in flight (an mbarrier per stage) while
 // the current tile is collided, so the SM has DRAM traffic outstanding
 // without holding it in registers. Pulls become shared-memory reads at fixed
@@ -316,6 +317,14 @@ void tma_variant_shape(int v, int* tx, int* ty) {
     }
     LBM_TMA_VARIANTS(LBM_SHAPE)
 #undef LBM_SHAPE
+}
+
+int tma_plain_partner(int v) {
+    int tx = 0, ty = 0;
+    tma_variant_shape(v, &tx, &ty);
+    for (int i = 0; i < kTileCount; ++i)
+        if (kTiles[i][0] == tx && kTiles[i][1] * kTiles[i][2] == ty) return i;
+    return -1;
 }
 
 int tma_blocks_per_sm(int v) {

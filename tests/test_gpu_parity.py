@@ -77,9 +77,12 @@ def test_fp32_matches_oracle(case, precision):
 
 @pytest.mark.parametrize("precision", ["fp32_dev", "fp64"])
 def test_every_tile_is_bitwise_identical(precision):
-    # includes the TMA-staged persistent FP32 variants, ragged tiles, walls
-    # and a lattice under 4 cells high (ghost frame refreshed separately)
-    specs = [small_spec(70, 45, walls=True), small_spec(19, 23), small_spec(5, 3), small_spec(130, 9)]
+    # includes the TMA-staged persistent FP32 variants (on the tiles two
+    # cells or more from every edge, beside the plain kernel on the others),
+    # ragged tiles, walls, and lattices under 4 cells high or narrower than
+    # a tile (periodic wrap of a pull onto the node itself or its neighbour)
+    specs = [small_spec(70, 45, walls=True), small_spec(19, 23), small_spec(5, 3), small_spec(130, 9),
+             small_spec(200, 44, seed=7), small_spec(1, 6, seed=8), small_spec(2, 1, seed=9)]
     ref = run_gpu(specs, precision, 5, tile=0)
     for t in range(1, lbm.lbm_tile_count()):
         try:
@@ -313,7 +316,7 @@ def test_tma_wait_timeout_reports_etimeout_and_context_recovers(monkeypatch):
     CTA records the timeout, waits for its copies and returns, and the host
     reports LBM_ETIMEOUT. A context with the normal settings then steps
     correctly."""
-    specs = [small_spec(64, 40, seed=21)]
+    specs = [small_spec(128, 40, seed=21)]  # has tiles two cells or more from every edge
     tma = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_TMA]
     if not tma:
         pytest.skip("no TMA variants")
@@ -448,9 +451,9 @@ def test_pinned_host_buffers_are_read_and_written_in_place():
 
 @pytest.mark.parametrize("precision", ["fp32_dev", "fp64"])
 def test_y_uniform_batch_matches_one_row_lattice(precision):
-    """A y-uniform field on 64 x 8 (main kernels, ghost images in the step)
-    and on 64 x 1 (a lattice under 4 cells: frames rewritten by the refresh
-    kernel) must evolve identically, row for row, bit for bit."""
+    """A y-uniform field on 64 x 8 and on 64 x 1 (one node high: every pull
+    along y wraps onto the node itself) must evolve identically, row for
+    row, bit for bit."""
     Tc = inputs.critical_temperature()
     c = inputs.coexistence(0.7)
     nx = 64
