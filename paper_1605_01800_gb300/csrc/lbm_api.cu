@@ -332,7 +332,8 @@ int build_tma(lbm_ctx* c, int tile_index) {
 }
 
 // Work-lists of one step: every tile of every lattice, lattices in creation
-// order, tiles row-major within a lattice. The pipelined and TMA variants
+// order, tiles row-major within a lattice (in the plain kernel's list, the
+// tiles of its general path come first). The pipelined and TMA variants
 // take the tiles at least two cells away from every edge of their lattice
 // (the pipelined ones only wall-free Carnahan-Starling tiles); the plain
 // kernel of the same node tile takes the rest.
@@ -387,6 +388,16 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     }
     if (tiles.size() > (size_t)0x7fffffff || fast.size() > (size_t)0x7fffffff || inner_tiles.size() > (size_t)0x7fffffff)
         return fail(LBM_EINVAL, "too many tiles");
+    // tiles that take the general path (walls nearby, partial tiles, other
+    // EOS kinds, lattices under 4 x 4) run longer than fast-path tiles: put
+    // them first, so that they start in the first wave instead of trailing
+    // the last one (every tile is independent: the order changes no result)
+    std::stable_partition(tiles.begin(), tiles.end(), [&](const Tile& t) {
+        const Geom& g = c->lats[t.lat].geom;
+        const bool full = t.x0 + tx <= g.nx && t.y0 + ty <= g.ny;
+        const bool fast = t.clear && full && g.nx >= 4 && g.ny >= 4 && c->lats[t.lat].desc.eos.kind == LBM_EOS_CS;
+        return !fast;
+    });
     std::vector<TileGeom> tgeo(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) tgeo[k] = TileGeom{c->lats[tiles[k].lat].geom, tiles[k]};
     Tile* d = nullptr;
