@@ -35,8 +35,11 @@ ALG_BYTES_FP32 = 72   # 9 reads + 9 writes of 4 B per node update
 ALG_BYTES_FP64 = 144
 WORKLOAD = "coexistence_batch"
 PROFILE = os.path.join(ROOT, "profiles", "step_fp32_coexistence_batch.md")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1605_01800_gb300", "csrc", f)
-                  for f in ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu", "lbm_step_pipe.cu")]
+# device sources of each step-kernel kind whose ncu traffic the profile records
+# (a pipelined step also launches the plain kernel on its other tiles)
+_PLAIN = ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu")
+KERNEL_SOURCES = {kind: [os.path.join(ROOT, "paper_1605_01800_gb300", "csrc", f) for f in files]
+                  for kind, files in (("plain", _PLAIN), ("pipelined", _PLAIN + ("lbm_step_pipe.cu",)))}
 
 
 def parse_args():
@@ -72,23 +75,23 @@ def run_profile(args):
     b.close()
 
 
-def kernel_source_hash():
+def kernel_source_hash(kind):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kind]:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(tile):
-    """DRAM bytes per launch of the step kernel with tile index `tile` from the
-    committed ncu summary, or None when the kernel source changed since that
-    capture or that tile was not captured."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(tile, kind):
+    """DRAM bytes of one step with tile index `tile` (a step kernel of `kind`,
+    "plain" or "pipelined") from the committed ncu summary, or None when that
+    kernel's source changed since the capture or the tile was not captured."""
+    if kind not in KERNEL_SOURCES or not os.path.exists(PROFILE):
         return None
     text = open(PROFILE).read()
-    m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_hash = re.search(r"kernel_source_sha\[%s\]:\s*([0-9a-f]+)" % kind, text)
     m_bytes = re.search(r"dram_bytes_per_launch\[%d\]:\s*([0-9.eE+]+)" % tile, text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(kind):
         return None
     return float(m_bytes.group(1))
 
@@ -417,7 +420,8 @@ def main():
     for v in large.values():
         v["frac"] = v["achieved_gbs"] / peak
     achieved = ALG_BYTES_FP32 * nodes / (ms_per_step * 1e-3) / 1e9
-    traffic = profiled_traffic(best_tile)
+    kinds = {lbm.LBM_TILE_PLAIN: "plain", lbm.LBM_TILE_PIPELINED: "pipelined"}
+    traffic = profiled_traffic(best_tile, kinds.get(lbm.lbm_tile_kind(best_tile)))
 
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,

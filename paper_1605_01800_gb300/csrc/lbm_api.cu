@@ -90,10 +90,10 @@ struct lbm_ctx {
     Phys<double>* d_phys_d = nullptr;
     Tile* d_tiles = nullptr;
     int n_tiles = 0;             // tiles of the plain kernel
-    // pipelined variants: the full wall-free tiles away from the lattice edges
-    // go to the persistent kernel (d_fast, n_fast, pipe_grid CTAs), the rest
-    // (d_tiles) to the plain kernel of the same node tile; TMA variants
-    // likewise take the tiles away from the edges (d_tma, n_tma)
+    // pipelined variants: the full wall-free tiles go to the persistent kernel
+    // (d_fast, n_fast, pipe_grid CTAs), the rest (d_tiles) to the plain kernel
+    // of the same node tile; TMA variants take the tiles two cells or more
+    // from every lattice edge (d_tma, n_tma), the plain kernel the rest
     TileGeom* d_tgeo = nullptr;  // d_tiles with their lattices' geometry (plain kernel)
     FastTile* d_fast = nullptr;
     int n_fast = 0;
@@ -333,10 +333,10 @@ int build_tma(lbm_ctx* c, int tile_index) {
 
 // Work-lists of one step: every tile of every lattice, lattices in creation
 // order, tiles row-major within a lattice (in the plain kernel's list, the
-// tiles of its general path come first). The pipelined and TMA variants
-// take the tiles at least two cells away from every edge of their lattice
-// (the pipelined ones only wall-free Carnahan-Starling tiles); the plain
-// kernel of the same node tile takes the rest.
+// tiles of its general path come first). The pipelined variants take the
+// full wall-free Carnahan-Starling tiles, the TMA variants the tiles two
+// cells or more from every edge of their lattice; the plain kernel of the
+// same node tile takes the rest.
 int build_tiles(lbm_ctx* c, int tile_index) {
     if (tile_index < 0 || tile_index >= total_tiles()) return fail(LBM_EINVAL, "no tile shape %d", tile_index);
     if (tile_index >= kTileCount && c->precision == LBM_FP64)
@@ -378,8 +378,9 @@ int build_tiles(lbm_ctx* c, int tile_index) {
                 }
                 // no pull of the tile or of its halo ring crosses an edge
                 const bool inner = x0 >= 2 && x0 + tx <= g.nx - 2 && y0 >= 2 && y0 + ty <= g.ny - 2;
-                if (pipe && clear && inner && L.desc.eos.kind == LBM_EOS_CS)
-                    fast.push_back(FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, {0, 0, 0}});
+                if (pipe && clear && full && g.nx >= 4 && g.ny >= 4 && L.desc.eos.kind == LBM_EOS_CS)
+                    fast.push_back(
+                        FastTile{g.f_off, (int)g.plane, g.pitch, g.nx, g.ny, l, x0, y0, inner ? 0 : 1, {0, 0}});
                 else if (tma && inner)
                     inner_tiles.push_back(Tile{l, x0, y0, clear ? 1 : 0});
                 else

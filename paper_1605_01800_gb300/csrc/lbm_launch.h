@@ -60,14 +60,13 @@ bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const
 
 // Persistent software-pipelined FP32 variants (lbm_step_pipe.cu); tile
 // indices kTileCount + tma_variant_count() + v. They take the full wall-free
-// tiles at least two cells away from every lattice edge (FastTile list:
-// fixed-offset pulls only); the other tiles of the step go through the plain
+// tiles (FastTile list); the other tiles of the step go through the plain
 // kernel of the same node tile (pipe_plain_partner) in a second launch.
 struct FastTile {
     long long f_off;       // plane 0 of the tile's lattice (element offset, both buffers)
     int plane, pitch, nx, ny;
-    int lat, x0, y0;
-    int pad[3];
+    int lat, x0, y0, edge; // edge: within two cells of a lattice edge (wrapped pulls)
+    int pad[2];
 };
 struct PipeArgs {
     const FastTile* fast;

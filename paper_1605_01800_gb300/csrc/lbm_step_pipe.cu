@@ -8,10 +8,11 @@
 // keeps two register sets: after the psi barrier of tile k it issues the
 // pulled loads of its next tile (own node pairs and its halo cell) and only
 // then does the force, the collision and the stores of tile k, so those loads
-// are in flight while it computes. Its tiles lie at least two cells from every
-// lattice edge, so every pull is a fixed offset. The other tiles (edge tiles,
-// partial tiles, walls, lattices under 4 x 4) go through step_kernel in a
-// second launch of the same step; the two launches write disjoint nodes.
+// are in flight while it computes. Tiles within two cells of a lattice edge
+// wrap the pulls that cross it, as in step_kernel's fast path. Tiles that
+// need the general path (partial tiles, walls, lattices under 4 x 4) go
+// through step_kernel in a second launch of the same step; the two launches
+// write disjoint nodes.
 #include "lbm_launch.h"
 #include "lbm_step.cuh"
 
@@ -24,8 +25,20 @@ __device__ __forceinline__ void pipe_load(const float* __restrict__ fin, const F
                                           bool has_h, int hcx, int hcy, F2 f[9], float fh[9]) {
     const float* __restrict__ base = fin + T.f_off;
     const int pitch = T.pitch, plane = T.plane;
-    pull_pair(base, plane, pitch, (T.y0 + ly0 + kGY) * pitch + T.x0 + lx + kGX, f);
-    if (has_h) pull_inner<float>(base, plane, pitch, (T.y0 - 1 + hcy + kGY) * pitch + T.x0 - 1 + hcx + kGX, fh);
+    const int x = T.x0 + lx, y = T.y0 + ly0;
+    const int c = (y + kGY) * pitch + x + kGX;
+    const int hx = T.x0 - 1 + hcx, hy = T.y0 - 1 + hcy;
+    if (T.edge) {
+        const int dxm = x == 0 ? T.nx - 1 : -1;
+        const int dxp = x == T.nx - 1 ? 1 - T.nx : 1;
+        const int rm = y == 0 ? (T.ny - 1) * pitch : -pitch;
+        const int rp2 = y + 1 == T.ny - 1 ? (1 - T.ny) * pitch : pitch;
+        pull_pair_wrap(base, plane, pitch, c, dxm, dxp, rm, rp2, f);
+        if (has_h) pull_node<float>(base, nullptr, plane, nbr_of(T.nx, T.ny, pitch, hx, hy), fh);
+    } else {
+        pull_pair(base, plane, pitch, c, f);
+        if (has_h) pull_inner<float>(base, plane, pitch, (hy + kGY) * pitch + hx + kGX, fh);
+    }
 }
 
 template <int TX, int TYT, int MINB, bool TABLE>
