@@ -199,12 +199,17 @@ int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes);
 
 /* Select the CTA tile of the step kernel by index into the built-in list
  * (lbm_tile_count() entries; lbm_tile_shape gives each node tile, lbm_tile_kind
- * the kernel that runs it: LBM_TILE_PLAIN, one CTA per tile; LBM_TILE_TMA,
- * TMA-staged persistent, FP32 and batches of at most 64 lattices;
- * LBM_TILE_PIPELINED, persistent with the next tile's loads in flight during
- * the collision, FP32, full wall-free tiles, the other tiles of the step by
- * the plain kernel of the same shape). Results are bitwise identical for
- * every tile. An FP32-only index on an FP64 context is LBM_EINVAL. */
+ * the kernel that runs it):
+ *   LBM_TILE_PLAIN      one CTA per tile;
+ *   LBM_TILE_TMA        TMA-staged persistent, FP32, batches of at most 64
+ *                       lattices; it takes the tiles two cells or more from
+ *                       every lattice edge, the plain kernel of the same shape
+ *                       the others;
+ *   LBM_TILE_PIPELINED  persistent with the next tile's loads in flight during
+ *                       the collision, FP32; it takes the full wall-free tiles,
+ *                       the plain kernel of the same shape the others.
+ * Results are bitwise identical for every tile. An FP32-only index on an FP64
+ * context is LBM_EINVAL. */
 #define LBM_TILE_PLAIN 0
 #define LBM_TILE_TMA 1
 #define LBM_TILE_PIPELINED 2
