@@ -135,6 +135,30 @@ typedef struct {
     int graph_chunk;           /* steps per CUDA-graph replay in lbm_step */
 } lbm_info_t;
 
+/* Where one lattice's current state lives on the device (lbm_state_view),
+ * for zero-copy access from other device code, e.g. a PyTorch tensor built
+ * through __cuda_array_interface__. Population a of node (x, y) (Eq. 1-5
+ * numbering, 0 <= x < nx, 0 <= y < ny) is element
+ *     a * plane + (y + y0) * pitch + (x + x0)
+ * of the array at `base`. Each element is f_a - w_a rho_ref with FP32
+ * deviation storage, and f_a with plain FP32 or FP64 storage. The frame
+ * around the nodes (the other rows and columns of each plane) holds no
+ * populations: no step reads it, so it may hold anything.
+ * The view describes the buffer that the next step reads; a step writes
+ * the other buffer and then reads from it, so query again after lbm_step.
+ * The memory belongs to the context (valid until lbm_destroy), and access
+ * is ordered with the context's stream by the caller (lbm_sync). */
+typedef struct {
+    void* base;          /* device address of plane 0 */
+    long long plane;     /* elements per plane = rows * pitch */
+    int pitch;           /* elements per row */
+    int rows;            /* rows per plane (ny plus the frame) */
+    int x0, y0;          /* stored column and row of node (0, 0) */
+    int elem_bytes;      /* 4 (FP32 storage) or 8 (FP64) */
+    int deviation;       /* 1 for FP32 deviation storage */
+    double rho_ref;      /* the deviation reference (0 for plain storage) */
+} lbm_state_view;
+
 /* Create a one-lattice context (the paper's single-domain runs, Sec. 3-4).
  * eps is the epsilon of Eq. 14; relax_rates the nine rates of Eq. 2. For
  * LBM_FP32_DEV the deviation reference is the minimum of the first density
@@ -227,6 +251,10 @@ int lbm_autotune(lbm_ctx* ctx, int steps, int* best_index, double* ms);
 
 /* Context introspection. */
 int lbm_info(lbm_ctx* ctx, lbm_info_t* info);
+
+/* Fill *view for lattice `lat` (see lbm_state_view). LBM_EINVAL for a null
+ * argument or a lattice index out of range. No device work, no sync. */
+int lbm_get_state_view(lbm_ctx* ctx, int lat, lbm_state_view* view);
 
 /* Largest ny accepted by lbm_total_mass_fp32_noalloc. */
 #define LBM_NOALLOC_MAX_NY 32768

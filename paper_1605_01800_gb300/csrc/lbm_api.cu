@@ -1221,6 +1221,24 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
     return LBM_OK;
 }
 
+int lbm_get_state_view(lbm_ctx* c, int lat, lbm_state_view* view) {
+    if (!view) return fail(LBM_EINVAL, "null argument");
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    const HostLattice& L = c->lats[lat];
+    const Geom& g = L.geom;
+    view->base = (char*)c->f[c->cur] + (size_t)g.f_off * c->elem;
+    view->plane = g.plane;
+    view->pitch = g.pitch;
+    view->rows = (int)(g.plane / g.pitch);
+    view->x0 = kGX;
+    view->y0 = kGY;
+    view->elem_bytes = c->elem;
+    view->deviation = c->precision == LBM_FP32_DEV ? 1 : 0;
+    view->rho_ref = c->precision == LBM_FP32_DEV ? L.rho_ref : 0.0;
+    return LBM_OK;
+}
+
 int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     if (!c || !info) return fail(LBM_EINVAL, "null argument");
     info->n_lattices = c->n;

@@ -39,7 +39,7 @@ EXPORTED = [
     "lbm_step", "lbm_read_moments", "lbm_read_moments_all", "lbm_total_mass", "lbm_status",
     "lbm_clear_status", "lbm_sync", "lbm_state_size", "lbm_save_state", "lbm_load_state",
     "lbm_tile_count", "lbm_tile_shape", "lbm_tile_kind", "lbm_set_tile", "lbm_autotune", "lbm_info",
-    "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc",
+    "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc", "lbm_get_state_view",
 ]
 
 
@@ -71,6 +71,12 @@ class lbm_info_t(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("kernel_launches", ctypes.c_ulonglong),
                 ("device_bytes", ctypes.c_size_t), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("n_tiles", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
+
+
+class lbm_state_view(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_void_p), ("plane", ctypes.c_longlong), ("pitch", ctypes.c_int),
+                ("rows", ctypes.c_int), ("x0", ctypes.c_int), ("y0", ctypes.c_int),
+                ("elem_bytes", ctypes.c_int), ("deviation", ctypes.c_int), ("rho_ref", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -122,6 +128,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_set_tile.argtypes = [_ctx, I]
     lib.lbm_autotune.argtypes = [_ctx, I, ctypes.POINTER(I), _dp]
     lib.lbm_info.argtypes = [_ctx, ctypes.POINTER(lbm_info_t)]
+    lib.lbm_get_state_view.argtypes = [_ctx, I, ctypes.POINTER(lbm_state_view)]
     lib.lbm_last_error.argtypes = []
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_total_mass_fp32_noalloc.argtypes = [_vp, I, I, ctypes.c_double, _vp, _vp, _vp]
@@ -268,6 +275,33 @@ def lbm_info(ctx) -> dict:
     info = lbm_info_t()
     _check(load().lbm_info(ctx, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in lbm_info_t._fields_}
+
+
+def lbm_get_state_view(ctx, lat) -> lbm_state_view:
+    v = lbm_state_view()
+    _check(load().lbm_get_state_view(ctx, lat, ctypes.byref(v)))
+    return v
+
+
+class StateArray:
+    """The nine stored planes of one lattice's current state, (9, rows, pitch),
+    exposed through ``__cuda_array_interface__`` (so that, e.g.,
+    ``torch.as_tensor(StateArray(ctx, i), device="cuda")`` is a zero-copy view);
+    node (x, y) is at ``[:, y + y0, x + x0]``. Only marshalling: the layout is the
+    one lbm_get_state_view reports."""
+
+    def __init__(self, ctx, lat):
+        v = lbm_get_state_view(ctx, lat)
+        self.view = v
+        self.x0, self.y0 = v.x0, v.y0
+        self.__cuda_array_interface__ = {
+            "shape": (9, v.rows, v.pitch),
+            "typestr": "<f4" if v.elem_bytes == 4 else "<f8",
+            "data": (v.base, False),
+            "strides": None,
+            "version": 3,
+            "stream": None,
+        }
 
 
 def lbm_last_error() -> str:

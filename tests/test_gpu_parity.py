@@ -572,3 +572,82 @@ def test_autotune_cache_measures_once_and_reuses(tmp_path):
     for a, b in zip(got, ref):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def _checkpoint_nodes(blob, specs, lat, elem):
+    """Node values of lattice `lat` from an lbm_save_state blob: a 16-byte
+    header, the step count, one rho_ref per lattice, then per lattice nine
+    planes of ny rows of round_up(nx, 32) elements (each lattice's block
+    rounded up to 64 elements)."""
+    off = 16 + 8 + 8 * len(specs)
+    dt = np.float32 if elem == 4 else np.float64
+    c_off = 0
+    for i, s in enumerate(specs):
+        cp = -(-s.nx // 32) * 32
+        if i == lat:
+            a = np.frombuffer(blob, dtype=dt, count=9 * s.ny * cp, offset=off + c_off * elem)
+            return a.reshape(9, s.ny, cp)[:, :, :s.nx]
+        c_off += -(-(9 * s.ny * cp) // 64) * 64
+    raise IndexError(lat)
+
+
+@pytest.mark.parametrize("precision", ["fp32_dev", "fp64"])
+def test_state_view_is_the_checkpointed_state(precision):
+    """lbm_get_state_view: a zero-copy torch view of each lattice's current
+    buffer holds, at the nodes, exactly what the checkpoint holds."""
+    torch = pytest.importorskip("torch")
+    specs = [small_spec(70, 45, walls=True), small_spec(200, 44, seed=7)]
+    b = lbm.Batch(specs, precision)
+    b.init()
+    b.step(5)
+    lbm.lbm_sync(b.ctx)
+    blob = lbm.lbm_save_state(b.ctx)
+    for i, s in enumerate(specs):
+        arr = lbm.StateArray(b.ctx, i)
+        v = arr.view
+        assert v.deviation == (1 if precision == "fp32_dev" else 0)
+        assert v.plane == v.rows * v.pitch and v.x0 + s.nx <= v.pitch and v.y0 + s.ny <= v.rows
+        t = torch.as_tensor(arr, device="cuda")
+        got = t[:, v.y0:v.y0 + s.ny, v.x0:v.x0 + s.nx].cpu().numpy()
+        assert np.array_equal(got, _checkpoint_nodes(blob, specs, i, v.elem_bytes))
+    b.close()
+
+
+def test_no_step_reads_the_frame():
+    """Periodic streaming wraps by index arithmetic: the frame around the
+    nodes of both distribution buffers may hold anything. Filled with NaN
+    there, every step-kernel kind (plain, TMA, pipelined) gives the same
+    bits as without."""
+    torch = pytest.importorskip("torch")
+    specs = [small_spec(70, 45, walls=True), small_spec(200, 44, seed=7), small_spec(5, 3)]
+    kinds = {}
+    for t in range(lbm.lbm_tile_count()):
+        kinds.setdefault(lbm.lbm_tile_kind(t), t)
+
+    def poison(b):
+        lbm.lbm_sync(b.ctx)
+        for i, s in enumerate(specs):
+            arr = lbm.StateArray(b.ctx, i)
+            v = arr.view
+            f = torch.as_tensor(arr, device="cuda")
+            f[:, :v.y0, :] = float("nan")
+            f[:, v.y0 + s.ny:, :] = float("nan")
+            f[:, :, :v.x0] = float("nan")
+            f[:, :, v.x0 + s.nx:] = float("nan")
+        torch.cuda.synchronize()
+
+    for tile in kinds.values():
+        ref = run_gpu(specs, "fp32_dev", 6, tile=tile)
+        b = lbm.Batch(specs, "fp32_dev")
+        lbm.lbm_set_tile(b.ctx, tile)
+        b.init()
+        poison(b)      # the buffer the first step reads
+        b.step(1)
+        poison(b)      # the other one
+        b.step(5)
+        got = [b.moments(i, allow_flags=True) for i in range(len(specs))]
+        assert all(b.status(i) == 0 for i in range(len(specs)))
+        b.close()
+        for a, c in zip(ref, got):
+            for x, y in zip(a, c):
+                assert np.array_equal(x, y), f"tile {tile}"
