@@ -651,3 +651,39 @@ def test_no_step_reads_the_frame():
         for a, c in zip(ref, got):
             for x, y in zip(a, c):
                 assert np.array_equal(x, y), f"tile {tile}"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dev"])
+def test_degenerate_solid_lattices(precision):
+    """A lattice that is solid everywhere, and one whose only fluid node is
+    walled in on all eight sides, in a batch beside an ordinary lattice.
+    The solid one reads out zero density and zero mass with no flags. The
+    walled-in node bounces back every link, and every neighbour in Eq. 7 takes
+    its own psi, so F = 0: it keeps its density, as in the oracle. The
+    ordinary lattice evolves as it does alone."""
+    solid_all = small_spec(8, 6, seed=3)
+    solid_all.solid = np.ones((6, 8), np.uint8)
+    lone = small_spec(5, 5, seed=4)
+    lone.solid = np.ones((5, 5), np.uint8)
+    lone.solid[2, 2] = 0
+    other = small_spec(37, 29, seed=5)
+    specs = [solid_all, lone, other]
+    steps = 7
+    b = lbm.Batch(specs, precision)
+    b.init()
+    b.step(steps)
+    got = [b.moments(i, allow_flags=True) for i in range(3)]
+    assert [b.status(i) for i in range(3)] == [0, 0, 0]
+    assert b.mass(0) == 0.0
+    b.close()
+    assert np.all(got[0][0] == 0.0) and np.all(np.isfinite(got[0][1]))
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    (orho, oux, ouy, _), _ = run_oracle(lone, steps)
+    assert got[1][0][2, 2] == pytest.approx(lone.rho[2, 2], rel=tol)
+    assert got[1][0][2, 2] == pytest.approx(orho[2, 2], rel=tol)
+    ulim = 1e-12 if precision == "fp64" else 1e-6
+    assert abs(got[1][1][2, 2]) < ulim and abs(got[1][2][2, 2]) < ulim
+    assert np.all(got[1][0][lone.solid == 1] == 0.0)
+    (alone,) = run_gpu([other], precision, steps)
+    for x, y in zip(got[2], alone):
+        assert np.array_equal(x, y)
