@@ -259,16 +259,24 @@ def test_droplet_128_3000_steps():
 
 
 def test_coexistence_batch_full_size():
-    """32 slabs 256x64: every lattice after 20 steps, FP32 deviation and FP64."""
+    """32 slabs 256x64: every lattice after 20 steps, FP32 deviation and FP64.
+    FP32 runs with every shape the benchmark's sweep can pick on this batch
+    (plain and pipelined kinds) and with the autotuner's choice."""
     specs = inputs.coexistence_batch()
     steps = 20
-    g32 = run_gpu(specs, "fp32_dev", steps)
+    b = lbm.Batch(specs, "fp32_dev")
+    b.init()
+    best, _ = lbm.lbm_autotune(b.ctx, 5)
+    b.close()
+    tiles = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) != lbm.LBM_TILE_TMA]
+    g32 = {t: run_gpu(specs, "fp32_dev", steps, tile=t) for t in sorted(set(tiles) | {best})}
     g64 = run_gpu(specs, "fp64", steps)
     for i, spec in enumerate(specs):
         (orho, oux, ouy, op), L = run_oracle(spec, steps)
         assert L.flags == 0
         assert rel_err(g64[i][0], orho) < 1e-12, i
-        assert rel_err(g32[i][0], orho) < 1e-4, i
+        for t, g in g32.items():
+            assert rel_err(g[i][0], orho) < 1e-4, (i, t)
 
 
 def test_coexistence_batch_mass_conserved():
@@ -296,10 +304,12 @@ def test_laplace_batch_full_size_sampled():
     smallest, a middle and the largest lattice."""
     specs = inputs.laplace_batch()
     steps = 4
-    g = run_gpu(specs, "fp32_dev", steps)
+    # the shapes the benchmark's larger-than-L2 workloads choose from
+    gs = {t: run_gpu(specs, "fp32_dev", steps, tile=t) for t in (1, 3, 5)}
     for i in (0, 23, 47):
         (orho, _, _, _), _ = run_oracle(specs[i], steps)
-        assert rel_err(g[i][0], orho) < 1e-4, i
+        for t, g in gs.items():
+            assert rel_err(g[i][0], orho) < 1e-4, (i, t)
 
 
 def test_cavitation_1024_full_size():
@@ -317,9 +327,10 @@ def test_collapse_walls_full_size():
     m = fluid(spec)
     (g64,) = run_gpu([spec], "fp64", steps)
     assert rel_err(g64[0], orho, m) < 1e-12
-    (g32,) = run_gpu([spec], "fp32_dev", steps)
-    assert rel_err(g32[0], orho, m) < 1e-4
-    assert np.all(g32[0][~m] == 0)
+    for t in (1, 3, 5):  # the shapes the benchmark chooses from on this lattice
+        (g32,) = run_gpu([spec], "fp32_dev", steps, tile=t)
+        assert rel_err(g32[0], orho, m) < 1e-4, t
+        assert np.all(g32[0][~m] == 0)
 
 
 def test_coexistence_batch_20000_steps_fp32_vs_fp64():
