@@ -69,6 +69,18 @@ def test_create_rejects_bad_parameters(kw, fragment):
     assert fragment in str(e.value)
 
 
+def test_create_rejects_an_empty_batch():
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create_batch([], lbm.LBM_FP32_DEV)
+    assert e.value.code == lbm.LBM_EINVAL
+
+
+def test_state_view_rejects_null_arguments():
+    lib = lbm.load()
+    v = lbm.lbm_state_view()
+    assert lib.lbm_get_state_view(None, 0, ctypes.byref(v)) == lbm.LBM_EINVAL
+
+
 def test_create_rejects_unknown_precision():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create_batch([_desc()], 7)

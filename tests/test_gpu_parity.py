@@ -698,3 +698,20 @@ def test_degenerate_solid_lattices(precision):
     (alone,) = run_gpu([other], precision, steps)
     for x, y in zip(got[2], alone):
         assert np.array_equal(x, y)
+
+
+def test_zero_steps_change_nothing_and_negative_steps_are_rejected():
+    specs = [small_spec(37, 29)]
+    b = lbm.Batch(specs, "fp32_dev")
+    b.init()
+    b.step(3)
+    before = lbm.lbm_save_state(b.ctx)
+    launches = b.info()["kernel_launches"]
+    b.step(0)
+    assert lbm.lbm_save_state(b.ctx) == before
+    assert b.info()["kernel_launches"] == launches and b.info()["steps"] == 3
+    with pytest.raises(lbm.LbmError) as e:
+        b.step(-1)
+    assert e.value.code == lbm.LBM_EINVAL
+    assert lbm.lbm_save_state(b.ctx) == before
+    b.close()
