@@ -123,8 +123,12 @@ struct lbm_ctx {
     double* d_scalar = nullptr;
     double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
     double* d_psi = nullptr;     // read-out scratch: one FP64 psi plane per lattice
-    unsigned* d_bad = nullptr;   // per-lattice invalid-input flags of the init kernel
-    unsigned* h_bad = nullptr;   // their page-locked host copy
+    // per-lattice invalid-input flags of the init kernel: page-locked host
+    // memory that the kernel writes through its mapped address (m_bad); a
+    // flag equal to bad_gen was set by the current init call
+    unsigned* h_bad = nullptr;
+    unsigned* m_bad = nullptr;
+    unsigned bad_gen = 0;
     std::vector<Phys<double>> phys_d;
     PhysTable<float>* h_table = nullptr;  // FP32 parameters as a kernel argument (n <= kParamLattices)
     size_t device_bytes = 0;
@@ -265,7 +269,6 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->d_scalar);
     cudaFree(c->d_io);
     cudaFree(c->d_psi);
-    cudaFree(c->d_bad);
     cudaFreeHost(c->h_bad);
     delete c;
 }
@@ -661,20 +664,19 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
     const double* k_ux = ux ? c->d_io + c->total_nodes : nullptr;
     const double* k_uy = uy ? c->d_io + 2 * c->total_nodes : nullptr;
     const LaunchSet ls = launch_set(c, lat0, n_lat);
-    CK(cudaMemsetAsync(c->d_bad, 0, c->n * sizeof(unsigned), c->stream));
+    if (++c->bad_gen == 0) c->bad_gen = 1;  // 0 is the value of a flag never set
     cudaError_t e;
     if (c->precision == LBM_FP64)
-        e = launch_init_f64(ls, k_rho, k_ux, k_uy, (double*)c->f[c->cur], c->d_bad, c->stream);
+        e = launch_init_f64(ls, k_rho, k_ux, k_uy, (double*)c->f[c->cur], c->m_bad, c->bad_gen, c->stream);
     else
-        e = launch_init_f32(ls, k_rho, k_ux, k_uy, (float*)c->f[c->cur], c->d_bad, c->stream);
+        e = launch_init_f32(ls, k_rho, k_ux, k_uy, (float*)c->f[c->cur], c->m_bad, c->bad_gen, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     c->launches += 1;
     // the host arrays may be pageable and the staging buffer is reused: wait,
     // then report invalid input found by the init kernel
-    CK(cudaMemcpyAsync(c->h_bad, c->d_bad, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int l = lat0; l < lat0 + n_lat; ++l)
-        if (c->h_bad[l])
+        if (c->h_bad[l] == c->bad_gen)
             return fail(LBM_EINVAL,
                         "lattice %d: a fluid density is not finite and > 0, or a velocity is not finite "
                         "(the lattice's state is undefined until the next successful init)", l);
@@ -800,11 +802,17 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (!rc) rc = dev_alloc(c, &c->d_scalar, sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->total_nodes * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_psi, ((size_t)c->total_elems / 9 + 64) * sizeof(double));
-    if (!rc) rc = dev_alloc(c, &c->d_bad, n * sizeof(unsigned));
-    if (!rc && cudaHostAlloc((void**)&c->h_bad, n * sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
+    if (!rc && cudaHostAlloc((void**)&c->h_bad, n * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         c->h_bad = nullptr;
         rc = fail(LBM_ENOMEM, "cudaHostAlloc(%zu bytes) failed", n * sizeof(unsigned));
+    }
+    if (!rc) {
+        memset(c->h_bad, 0, n * sizeof(unsigned));
+        if (cudaHostGetDevicePointer((void**)&c->m_bad, c->h_bad, 0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(LBM_ECUDA, "no device address for the page-locked flag buffer");
+        }
     }
     if (rc) {
         free_ctx(c);

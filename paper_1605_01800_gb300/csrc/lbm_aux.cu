@@ -29,12 +29,14 @@ __device__ __forceinline__ double feq(int a, double rho, double ux, double uy) {
 // streams into, or f_eq_bbar(y) when y + e_b is solid (the reflected link).
 // With u = 0 (ux, uy null) f_eq_b = w_b rho, and the stored deviation is
 // w_b (rho - rho_ref). Invalid input (a fluid density that is not finite and
-// > 0, a non-finite velocity) sets bad[lat].
+// > 0, a non-finite velocity) sets bad[lat] = gen: `bad` is the host's
+// page-locked flag array, mapped, and gen identifies the host call, so the
+// flags need no clearing and no copy back.
 template <typename T>
 __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                             int lat0, const double* __restrict__ rho, const double* __restrict__ ux,
                             const double* __restrict__ uy, const uint8_t* __restrict__ mask_base,
-                            T* __restrict__ f_base, unsigned* __restrict__ bad) {
+                            T* __restrict__ f_base, unsigned* __restrict__ bad, unsigned gen) {
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const double rho_ref = phys[lat].rho_ref;
@@ -70,7 +72,7 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
         }
         store_node<T>(f, g, x, y, out);
     }
-    if (invalid) atomicOr(&bad[lat], 1u);
+    if (invalid) bad[lat] = gen;
 }
 
 // Pulled distribution of node (x, y) as stored (f_a - w_a rho_ref, or f_a
@@ -246,9 +248,9 @@ dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
 
 template <typename T>
 cudaError_t init_impl(const LaunchSet& L, const double* rho, const double* ux, const double* uy,
-                      T* f, unsigned* bad, cudaStream_t s) {
+                      T* f, unsigned* bad, unsigned gen, cudaStream_t s) {
     init_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(
-        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad);
+        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad, gen);
     return cudaGetLastError();
 }
 
@@ -285,12 +287,12 @@ cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T*
 }  // namespace
 
 cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, float* f, unsigned* bad, cudaStream_t s) {
-    return init_impl<float>(L, rho, ux, uy, f, bad, s);
+                            const double* uy, float* f, unsigned* bad, unsigned gen, cudaStream_t s) {
+    return init_impl<float>(L, rho, ux, uy, f, bad, gen, s);
 }
 cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, double* f, unsigned* bad, cudaStream_t s) {
-    return init_impl<double>(L, rho, ux, uy, f, bad, s);
+                            const double* uy, double* f, unsigned* bad, unsigned gen, cudaStream_t s) {
+    return init_impl<double>(L, rho, ux, uy, f, bad, gen, s);
 }
 cudaError_t launch_density_f32(const LaunchSet& L, const float* f, double* rho, cudaStream_t s) {
     return density_impl<float>(L, f, rho, s);

@@ -100,11 +100,12 @@ struct LaunchSet {
 
 // Initial state: f_a such that the next pull gathers f_eq(rho, u) at every
 // fluid node. rho/ux/uy are device arrays indexed by geom.node_off + y*nx + x
-// (ux/uy may be null for u = 0). bad[lat] is set to 1 for invalid input.
+// (ux/uy may be null for u = 0). bad[lat] is set to gen for invalid input
+// (bad: a device-visible address, e.g. mapped page-locked host memory).
 cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, float* f, unsigned* bad, cudaStream_t s);
+                            const double* uy, float* f, unsigned* bad, unsigned gen, cudaStream_t s);
 cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
-                            const double* uy, double* f, unsigned* bad, cudaStream_t s);
+                            const double* uy, double* f, unsigned* bad, unsigned gen, cudaStream_t s);
 
 // rho, v (Eq. 6), p (Eq. 10) into device arrays indexed like the init inputs
 // (all four required), computed in FP64 from the stored distribution; psi is
