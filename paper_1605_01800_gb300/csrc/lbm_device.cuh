@@ -172,12 +172,16 @@ __device__ __forceinline__ T ld_pop(const T* __restrict__ p, int i, int n) {
 #endif
     return p[i];
 }
+// Populations are stored with the streaming hint (evict first): the step
+// never reads what it writes, so L2 keeps the lines it reads, which
+// neighbouring tiles read again for their halos (1-3% on batches larger than
+// L2, no change on the bench batch).
 template <typename T>
 __device__ __forceinline__ void st_pop(T* __restrict__ p, int i, int n, T v) {
 #ifdef LBM_DEBUG
     if (i < 0 || i >= n) return;
 #endif
-    p[i] = v;
+    __stcs(p + i, v);
 }
 __device__ __forceinline__ uint8_t ld_mask(const uint8_t* __restrict__ m, int i, int n) {
 #ifdef LBM_DEBUG
