@@ -306,3 +306,57 @@ def test_y_uniform_field_evolves_as_the_one_row_lattice():
     for a, b in zip(runs[0], runs[1]):
         for row in b:
             assert np.array_equal(row, a[0])
+
+
+# ------------------------------------------------------------------ read-out velocity (Eq. 6)
+
+def test_readout_velocity_hand_computed_three_node_row():
+    # A 3 x 1 periodic row with given populations and psi of Eq. 12 at e = 0,
+    # psi = exp(-1/rho), worked out by hand: every y-neighbour of a node is
+    # the node's own row, so in Eq. 7 the axis term gives
+    # (1/3)(psi_{i+1} - psi_{i-1}) and the four diagonals (1/12) * 2 times the
+    # same difference, g_x = (psi_{i+1} - psi_{i-1}) / 2, g_y = 0, and
+    # F = -G psi_i g. Eq. 6: v = (sum_a e_a f_a + F/2) / rho. A dropped or
+    # doubled F/2 misses by |F_x| / (2 rho) > 1e-2 here.
+    rng = np.random.default_rng(66)
+    nx, G = 3, -1.0
+    f = rng.uniform(0.05, 0.15, size=(9, 1, nx)) * np.array([1.0, 3.0, 8.0])
+    L = d2q9.Lattice(nx, 1, G=G, eps=0.0, eos="psi_exp")
+    L.f[:] = f
+    rho, ux, uy, _ = L.moments()
+    r = f[:, 0, :].sum(axis=0)
+    psi = np.exp(-1.0 / r)
+    jx = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8])[0]
+    jy = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8])[0]
+    for i in range(nx):
+        gx = 0.5 * (psi[(i + 1) % nx] - psi[(i - 1) % nx])
+        Fx = -G * psi[i] * gx
+        assert abs(Fx) / (2 * r[i]) > 1e-2
+        assert rho[0, i] == pytest.approx(r[i], rel=1e-15)
+        assert ux[0, i] == pytest.approx((jx[i] + 0.5 * Fx) / r[i], rel=1e-13, abs=1e-16)
+        assert uy[0, i] == pytest.approx(jy[i] / r[i], rel=1e-13, abs=1e-16)
+
+
+@pytest.mark.parametrize("tr,eps", [(0.8, 1.0), (0.7, 1.86)])
+def test_readout_velocity_vanishes_at_steady_flat_interface(tr, eps):
+    # At a steady, mirror-symmetric flat interface the discrete mass flux
+    # through every link is zero, which makes the post-collision momentum the
+    # negative of the pre-collision one, j* = -j. The collision sends j to
+    # j + F (Eq. 3 with Eq. 6), so j = -F/2 and the velocity of Eq. 6,
+    # (j + F/2)/rho, is zero to rounding, while j/rho alone (a dropped F/2)
+    # or (j + F)/rho (a doubled one) is |F|/(2 rho), about 0.1 in the vapour.
+    Tc, _, _ = thermo.critical_point()
+    rg, rl, _ = thermo.maxwell(tr * Tc)
+    nx = 64
+    x = np.arange(nx, dtype=float)
+    prof = rg + 0.5 * (rl - rg) * (np.tanh(2 * (x - nx / 4) / 5) - np.tanh(2 * (x - 3 * nx / 4) / 5))
+    s = [1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1 / 0.6, 1 / 0.6]
+    L = d2q9.Lattice(nx, 1, T=tr * Tc, s=s, eps=eps)
+    L.init(prof[None, :])
+    L.step(20000)
+    assert L.flags == 0
+    rho, ux, uy, _ = L.moments()
+    jx = np.tensordot(EX, L.f, 1)
+    assert np.abs(jx / rho).max() > 0.05
+    assert np.abs(ux).max() < 1e-9
+    assert np.abs(uy).max() < 1e-15
