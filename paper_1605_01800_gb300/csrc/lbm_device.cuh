@@ -398,9 +398,12 @@ __device__ __forceinline__ void set_lane(F2& a, int i, float x) {
     if (i == 0) a.v.x = x; else a.v.y = x;
 }
 
+// Density sum of the FP32 path: f_0 plus the eight moving populations in
+// the association ((f1 + f3) + (f2 + f4)) + ((f5 + f7) + (f6 + f8)), whose
+// partial sums are also the pair sums of m = M f (vcollide).
 template <class V>
 __device__ __forceinline__ V vsum8(const V f[9]) {
-    return ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+    return ((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
 }
 template <class V>
 __device__ __forceinline__ V vsum9(const V f[9]) {
@@ -513,8 +516,9 @@ __device__ __forceinline__ void vcollide(V f[9], V rho, V drho, V Fx, V Fy, V g2
     const V p57 = f[5] + f[7], p68 = f[6] + f[8];
     const V a14 = p13 + p24;
     const V a58 = p57 + p68;
-    const V m1 = vfma(two, a58, splat<V>(0.0f) - vfma(four, f[0], a14));
-    const V m2 = vfma(four, f[0], a58) - two * a14;
+    const V f0 = f[0];
+    const V m1 = vfma(two, a58, splat<V>(0.0f) - vfma(four, f0, a14));
+    const V m2 = vfma(four, f0, a58) - two * a14;
     const V m4 = (d57 - d68) - two * sx;
     const V m6 = (d57 + d68) - two * sy;
     const V m7 = p13 - p24;
@@ -562,8 +566,19 @@ __device__ __forceinline__ void vcollide(V f[9], V rho, V drho, V Fx, V Fy, V g2
     f[6] = ((diag - qx) + qy) - a8;
     f[7] = ((diag - qx) - qy) + a8;
     f[8] = ((diag + qx) - qy) - a8;
-    // f*_0 as the remainder of the conserved density (see collide)
-    f[0] = drho - vsum8(f);
+    // f*_0: the rest population takes the difference between the moving
+    // populations the node received and those it sends on,
+    //   f*_0 = f_0 + (a14 - b14) + (a58 - b58),
+    // which in exact arithmetic is drho - sum_{a>=1} f*_a (collide). Near
+    // rest the two differences are exact (Sterbenz) and small, so the only
+    // rounding of the node's mass is that of the last addition, instead of
+    // the roundings of the two eight-term sums in drho - sum8(f*). In a
+    // steady field (a bulk phase, a flat interface) each step repeats the
+    // same roundings, so those made the mass drift linearly (2e-6 over 2000
+    // steps of the slab batch; 2e-8 in this form).
+    const V b14 = (f[1] + f[3]) + (f[2] + f[4]);
+    const V b58 = (f[5] + f[7]) + (f[6] + f[8]);
+    f[0] = f0 + ((a14 - b14) + (a58 - b58));
 }
 
 // Force sum g = sum_a w_a psi(x + e_a) e_a of Eq. 7 from the nine psi values

@@ -13,10 +13,10 @@ namespace lbm {
 // per thread in y, minimum resident CTAs per SM}; the node tile is
 // TX x (TYT * RY). Every shape computes bitwise the same result; they differ
 // only in speed.
-constexpr int kTileCount = 9;
+constexpr int kTileCount = 8;
 constexpr int kTiles[kTileCount][4] = {
-    {32, 8, 2, 4}, {32, 4, 2, 7}, {64, 4, 2, 4}, {32, 4, 4, 5}, {32, 2, 4, 10},
-    {32, 4, 2, 8}, {32, 8, 4, 1}, {64, 2, 4, 5}, {128, 2, 2, 4},
+    {32, 8, 2, 4}, {32, 4, 2, 7}, {64, 4, 2, 4}, {32, 4, 4, 5},
+    {32, 4, 4, 4}, {32, 4, 2, 8}, {32, 4, 2, 6}, {32, 8, 2, 3},
 };
 
 template <typename T>

@@ -25,16 +25,14 @@ cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& 
                    : launch_tile<64, 4, 2, 4, false>(n_tiles, args, nullptr, s);
     case 3: return table ? launch_tile<32, 4, 4, 5, true>(n_tiles, args, table, s)
                    : launch_tile<32, 4, 4, 5, false>(n_tiles, args, nullptr, s);
-    case 4: return table ? launch_tile<32, 2, 4, 10, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 2, 4, 10, false>(n_tiles, args, nullptr, s);
+    case 4: return table ? launch_tile<32, 4, 4, 4, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 4, 4, 4, false>(n_tiles, args, nullptr, s);
     case 5: return table ? launch_tile<32, 4, 2, 8, true>(n_tiles, args, table, s)
                    : launch_tile<32, 4, 2, 8, false>(n_tiles, args, nullptr, s);
-    case 6: return table ? launch_tile<32, 8, 4, 1, true>(n_tiles, args, table, s)
-                   : launch_tile<32, 8, 4, 1, false>(n_tiles, args, nullptr, s);
-    case 7: return table ? launch_tile<64, 2, 4, 5, true>(n_tiles, args, table, s)
-                   : launch_tile<64, 2, 4, 5, false>(n_tiles, args, nullptr, s);
-    case 8: return table ? launch_tile<128, 2, 2, 4, true>(n_tiles, args, table, s)
-                   : launch_tile<128, 2, 2, 4, false>(n_tiles, args, nullptr, s);
+    case 6: return table ? launch_tile<32, 4, 2, 6, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 4, 2, 6, false>(n_tiles, args, nullptr, s);
+    case 7: return table ? launch_tile<32, 8, 2, 3, true>(n_tiles, args, table, s)
+                   : launch_tile<32, 8, 2, 3, false>(n_tiles, args, nullptr, s);
     default: return cudaErrorInvalidValue;
     }
 }

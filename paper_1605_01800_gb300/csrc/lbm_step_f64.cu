@@ -17,11 +17,10 @@ cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>&
     case 1: return launch_tile<32, 4, 2>(n_tiles, args, s);
     case 2: return launch_tile<64, 4, 2>(n_tiles, args, s);
     case 3: return launch_tile<32, 4, 4>(n_tiles, args, s);
-    case 4: return launch_tile<32, 2, 4>(n_tiles, args, s);
+    case 4: return launch_tile<32, 4, 4>(n_tiles, args, s);
     case 5: return launch_tile<32, 4, 2>(n_tiles, args, s);
-    case 6: return launch_tile<32, 8, 4>(n_tiles, args, s);
-    case 7: return launch_tile<64, 2, 4>(n_tiles, args, s);
-    case 8: return launch_tile<128, 2, 2>(n_tiles, args, s);
+    case 6: return launch_tile<32, 4, 2>(n_tiles, args, s);
+    case 7: return launch_tile<32, 8, 2>(n_tiles, args, s);
     default: return cudaErrorInvalidValue;
     }
 }

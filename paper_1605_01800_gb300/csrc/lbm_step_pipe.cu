@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
 }
 
 // Pipelined shapes {TX, TYT, MINB}; the node tile is TX x 2 TYT.
-constexpr int kPipeShapes[][3] = {{32, 4, 4}, {32, 4, 5}, {32, 8, 2}, {64, 4, 2}};
+constexpr int kPipeShapes[][3] = {{32, 4, 4}, {32, 8, 2}, {64, 4, 2}};
 constexpr int kPipeCount = sizeof(kPipeShapes) / sizeof(kPipeShapes[0]);
 
 template <int TX, int TYT, int MINB>
@@ -157,7 +157,7 @@ int pipe_plain_partner(int v) {
     return -1;
 }
 
-#define LBM_PIPE_CASES(X) X(0, 32, 4, 4) X(1, 32, 4, 5) X(2, 32, 8, 2) X(3, 64, 4, 2)
+#define LBM_PIPE_CASES(X) X(0, 32, 4, 4) X(1, 32, 8, 2) X(2, 64, 4, 2)
 
 int pipe_blocks_per_sm(int v, bool table) {
     switch (v) {

@@ -19,7 +19,7 @@ def _profile_hash(kind):
 
 
 def test_profiled_traffic_matches_the_committed_profile():
-    for kind, tile in (("plain", 1), ("pipelined", 13)):
+    for kind, tile in (("plain", 1), ("pipelined", 12)):
         v = bench.profiled_traffic(tile, kind)
         if _profile_hash(kind) != bench.kernel_source_hash(kind):
             assert v is None, kind  # counters taken on other sources are not reported
@@ -31,12 +31,21 @@ def test_profiled_traffic_matches_the_committed_profile():
     assert bench.profiled_traffic(12345, "plain") is None  # tile not captured
 
 
-def test_profiled_traffic_is_null_once_the_sources_change(monkeypatch):
+def test_profiled_traffic_is_null_once_the_sources_change(monkeypatch, tmp_path):
+    # a summary recorded on the current sources of both kinds: each kind's
+    # figure is reported until that kind's own sources change
+    prof = tmp_path / "profile.md"
+    prof.write_text("kernel_source_sha[plain]: %s\nkernel_source_sha[pipelined]: %s\n"
+                    "dram_bytes_per_launch[1]: 1.9e7\ndram_bytes_per_launch[13]: 1.95e7\n"
+                    % (bench.kernel_source_hash("plain"), bench.kernel_source_hash("pipelined")))
+    monkeypatch.setattr(bench, "PROFILE", str(prof))
+    assert bench.profiled_traffic(1, "plain") == 1.9e7
+    assert bench.profiled_traffic(13, "pipelined") == 1.95e7
     real = bench.kernel_source_hash
     monkeypatch.setattr(bench, "kernel_source_hash",
                         lambda kind: "0" * 16 if kind == "plain" else real(kind))
     assert bench.profiled_traffic(1, "plain") is None
-    assert bench.profiled_traffic(13, "pipelined") is not None
+    assert bench.profiled_traffic(13, "pipelined") == 1.95e7
 
 
 class _FakeSmi:
