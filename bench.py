@@ -11,12 +11,16 @@ Timing: the working set (37.7 MB) fits in the 129 MB L2, so before every timed
 step (outside the timed events) a 256 MiB buffer is written and another 256 MiB
 buffer is read (evicting the written lines, so their write-back does not land
 in the timed step); each step is timed alone with CUDA events on the library's
-stream. The FP64-storage path
-(the plain comparator) is timed the same way. `e2e` times the public C ABI
-with host buffers: upload of every density field, one step, download of every
-density field. `cpu_baseline` times the FP64 CPU oracle on a bounded sample.
-Under torchrun every rank advances its own copy of the batch (weak scaling, no
-collective on the data path).
+stream. The FP64-storage path (the plain comparator) is timed the same way.
+`sustained` times back-to-back steps (CUDA-graph replay, events around the
+whole replay, no flush) on workloads larger than L2, among them the 4096^2
+lattice (1.2 GB) on which the sustained HBM fraction is measured. `e2e` times
+the public C ABI with host buffers: upload of every density field, one step,
+download of every density field. `cpu_baseline` times the FP64 CPU oracle on a
+bounded sample, on every host core. Under torchrun every rank advances its own
+copy of the batch (weak scaling, no collective on the data path), and the
+48-lattice Laplace batch is also split across the ranks by node count
+(`sharded`, strong scaling).
 """
 import argparse
 import hashlib
@@ -35,6 +39,9 @@ ALG_BYTES_FP32 = 72   # 9 reads + 9 writes of 4 B per node update
 ALG_BYTES_FP64 = 144
 WORKLOAD = "coexistence_batch"
 PROFILE = os.path.join(ROOT, "profiles", "step_fp32_coexistence_batch.md")
+# ncu DRAM bytes of one step of the sustained workloads (same summary format)
+SUSTAINED_PROFILES = {"roofline_4096": os.path.join(ROOT, "profiles", "step_fp32_roofline_4096.md")}
+SUSTAINED = ("laplace_batch", "collapse_2048x1024", "roofline_4096", "collapse_x8")
 # device sources of each step-kernel kind whose ncu traffic the profile records
 # (a pipelined step also launches the plain kernel on its other tiles)
 _PLAIN = ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu")
@@ -82,13 +89,15 @@ def kernel_source_hash(kind):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(tile, kind):
+def profiled_traffic(tile, kind, profile=None):
     """DRAM bytes of one step with tile index `tile` (a step kernel of `kind`,
-    "plain" or "pipelined") from the committed ncu summary, or None when that
-    kernel's source changed since the capture or the tile was not captured."""
-    if kind not in KERNEL_SOURCES or not os.path.exists(PROFILE):
+    "plain" or "pipelined") from a committed ncu summary (default: the bench
+    workload's), or None when that kernel's source changed since the capture
+    or the tile was not captured."""
+    profile = profile or PROFILE
+    if kind not in KERNEL_SOURCES or not os.path.exists(profile):
         return None
-    text = open(PROFILE).read()
+    text = open(profile).read()
     m_hash = re.search(r"kernel_source_sha\[%s\]:\s*([0-9a-f]+)" % kind, text)
     m_bytes = re.search(r"dram_bytes_per_launch\[%d\]:\s*([0-9.eE+]+)" % tile, text)
     if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(kind):
@@ -104,17 +113,21 @@ def measured_peak_hbm():
 
 
 class ClockSampler:
+    """nvidia-smi samples of the SM clock, its limit, the throttle reasons and
+    the GPU utilisation, taken every `period_ms` until stop(); the summary
+    gives the median SM clock over the samples under load (utilisation of
+    50% or more; all samples when none is) and every throttle reason seen."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=50):
         self.proc = None
         self.gpu = gpu_index
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -128,7 +141,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, smax, reasons = [], [], set()
+        sm, smax, loaded, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
@@ -139,13 +152,18 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                if float(parts[9]) >= 50.0:
+                    loaded.append(sm[-1])
+            except (IndexError, ValueError):
+                pass
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median(loaded or sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "samples_under_load": len(loaded), "reasons": sorted(reasons)}
 
 
 def dist_setup(args):
@@ -155,9 +173,18 @@ def dist_setup(args):
     return world, rank, local
 
 
-def time_oracle(specs, seconds, min_steps=1):
-    """FP64 oracle over the whole batch, whole time steps until `seconds` pass."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle(specs, seconds, threads=1, min_steps=1):
+    """FP64 oracle over the whole batch on `threads` host threads, whole time
+    steps until `seconds` pass; returns (MLUPS, steps, seconds, threads used)."""
     from oracle import d2q9
+    threads = threads if d2q9.set_threads(threads) else 1
     lats = []
     for s in specs:
         L = d2q9.Lattice(s.nx, s.ny, a=s.a, b=s.b, R=s.R, T=s.T, G=s.G, s=s.s, eps=s.eps, solid=s.solid)
@@ -173,7 +200,8 @@ def time_oracle(specs, seconds, min_steps=1):
         el = time.perf_counter() - t0
         if steps >= min_steps and el >= seconds:
             break
-    return nodes * steps / el / 1e6, steps, el
+    d2q9.set_threads(1)
+    return nodes * steps / el / 1e6, steps, el, threads
 
 
 def run_reference(args, budget_s=150.0):
@@ -188,6 +216,8 @@ def run_reference(args, budget_s=150.0):
     from paper_1605_01800_gb300 import inputs
     specs = inputs.coexistence_batch()
     from oracle import d2q9
+    cores = host_cores()
+    cores = cores if d2q9.set_threads(cores) else 1
     lats = []
     for s in specs:
         L = d2q9.Lattice(s.nx, s.ny, a=s.a, b=s.b, R=s.R, T=s.T, G=s.G, s=s.s, eps=s.eps, solid=s.solid)
@@ -214,8 +244,9 @@ def run_reference(args, budget_s=150.0):
     updates = sum(one_step() for _ in range(args.steps))
     el = time.perf_counter() - t0
     mlups = updates / el / 1e6
+    d2q9.set_threads(1)
     sample = (f"{args.steps} steps of {per_step} of the {len(lats)} lattices each (round-robin), "
-              f"{updates} node updates in {el:.1f} s, single thread")
+              f"{updates} node updates in {el:.1f} s, {cores} thread(s) (OpenMP over the nodes of a lattice)")
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -223,7 +254,7 @@ def run_reference(args, budget_s=150.0):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattices": len(specs), "nx": 256, "ny": 64,
                    "nodes_per_step": per_step * specs[0].nodes, "precision": "fp64 CPU oracle"},
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -250,6 +281,37 @@ def timed_steps(torch, ctx, lbm, stream, flush, steps):
             e1.record(stream)
     stream.synchronize()
     return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def sustained_steps(torch, lbm, specs, stream, tiles, steps=256, warm=32):
+    """Back-to-back steps of one batch on its own, no flush: CUDA-graph replay
+    of `steps` steps with CUDA events around the whole replay, for the fastest
+    of `tiles` (each tried on 64 steps from a fresh state). Returns
+    (ms per step, tile index, {tile: ms per step of the trial})."""
+    b = lbm.Batch(specs, "fp32_dev", stream=stream)
+
+    def replay(n):
+        with torch.cuda.stream(stream):
+            lbm.lbm_step(b.ctx, warm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lbm.lbm_step(b.ctx, n)
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    trial = {}
+    for t in tiles:
+        b.init()
+        lbm.lbm_set_tile(b.ctx, t)
+        trial[t] = replay(64)
+    best = min(trial, key=trial.get)
+    b.init()
+    lbm.lbm_set_tile(b.ctx, best)
+    ms = replay(steps)
+    lbm.lbm_sync(b.ctx, allow_flags=True)
+    b.close()
+    return ms, best, trial
 
 
 def main():
@@ -287,14 +349,29 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(v):
+        if world > 1:
+            t = torch.tensor([v], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            v = float(t.item())
+        return v
+
+    # clocks over the GPU-busy part of the run: the tile sweep, the timed
+    # steps and the sustained runs (the timed steps alone last milliseconds)
+    clocks = ClockSampler(dev)
+
     # ---- FP32 deviation storage (the product path)
     b32 = lbm.Batch(specs, "fp32_dev", stream=stream)
     b32.init()
-    # tile shape: the fastest of the library's shapes on flushed single steps
-    # (after a warm-up, so the first shape measured pays no first-launch cost)
+    # tile shape: the fastest of the plain and pipelined shapes on flushed
+    # single steps (after a warm-up, so the first shape measured pays no
+    # first-launch cost); the TMA-staged shapes run at about half the speed
+    # and are not tried
     timed_steps(torch, b32.ctx, lbm, stream, flush, 30)
+    sweep = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) != lbm.LBM_TILE_TMA]
+    plain = [t for t in sweep if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_PLAIN]
     tile_ms = {}
-    for t in range(lbm.lbm_tile_count()):
+    for t in sweep:
         lbm.lbm_set_tile(b32.ctx, t)
         tile_ms[t] = statistics.mean(timed_steps(torch, b32.ctx, lbm, stream, flush, 60))
     best_tile = min(tile_ms, key=tile_ms.get)
@@ -302,19 +379,13 @@ def main():
     b32.init()
     timed_steps(torch, b32.ctx, lbm, stream, flush, max(args.warmup, 3))
     launches0 = b32.info()["kernel_launches"]
-    clocks = ClockSampler(dev)
     barrier()
     t_wall0 = time.perf_counter()
     ms = timed_steps(torch, b32.ctx, lbm, stream, flush, args.steps)
     barrier()
     t_wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
     launches = b32.info()["kernel_launches"] - launches0
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms))
     ms_per_step = total_ms / args.steps
     mlups = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
     lbm.lbm_sync(b32.ctx)
@@ -328,6 +399,41 @@ def main():
         e1.record(stream)
     stream.synchronize()
     l2_mlups = nodes * 256 / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    # ---- sustained steps on workloads larger than L2 (no flush needed)
+    peak, peak_kind = measured_peak_hbm()
+    kinds = {lbm.LBM_TILE_PLAIN: "plain", lbm.LBM_TILE_PIPELINED: "pipelined"}
+    sustained = {}
+    for name in SUSTAINED:
+        lspecs = inputs.WORKLOADS[name]()
+        lnodes = sum(s.nodes for s in lspecs)
+        lms, lt, trial = sustained_steps(torch, lbm, lspecs, stream, plain)
+        gbs = ALG_BYTES_FP32 * lnodes / (lms * 1e-3) / 1e9
+        entry = {"nodes": lnodes, "working_set_bytes": 2 * 36 * lnodes, "tile": lbm.lbm_tile_shape(lt),
+                 "tile_index": lt, "steps": 256, "ms_per_step": lms, "MLUPS": lnodes / (lms * 1e-3) / 1e6,
+                 "achieved_gbs": gbs, "frac": gbs / peak,
+                 "tile_trial_us": {str(t): round(1e3 * v, 2) for t, v in trial.items()}}
+        if name in SUSTAINED_PROFILES:
+            tr = profiled_traffic(lt, kinds.get(lbm.lbm_tile_kind(lt)), SUSTAINED_PROFILES[name])
+            entry["dram_bytes_per_node"] = None if tr is None else tr / lnodes
+        sustained[name] = entry
+        del lspecs
+    clk = clocks.stop()
+
+    # ---- the Laplace batch split across the ranks by node count (strong
+    # scaling; one rank alone advances the whole batch)
+    sharded = None
+    if world > 1:
+        from paper_1605_01800_gb300 import sharding
+        lspecs = inputs.laplace_batch()
+        mine = sharding.shard(lspecs, rank, world)
+        barrier()
+        sms = sustained_steps(torch, lbm, mine, stream, [3])[0] if mine else 0.0
+        sms = max_over_ranks(sms)
+        lnodes = sum(s.nodes for s in lspecs)
+        sharded = {"workload": "laplace_batch", "lattices": len(lspecs), "ranks": world,
+                   "ms_per_step": sms, "MLUPS": lnodes / (sms * 1e-3) / 1e6,
+                   "note": "LPT shares by node count, each rank steps its own share, max over ranks"}
 
     # ---- e2e through the C ABI with host buffers
     rho_in = torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
@@ -345,11 +451,7 @@ def main():
         lbm.lbm_step(b32.ctx, 1)
         lbm.lbm_read_moments_all(b32.ctx, rho_out)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_mlups = world * nodes * e2e_steps / e2e_s / 1e6
     b32.close()
 
@@ -395,32 +497,7 @@ def main():
     copy_gbs = 2 * src.numel() * 4 / (copy_ms * 1e-3) / 1e9
     del src, dst
 
-    # ---- context: workloads larger than L2 (one FP32 buffer 75-81 MB, both 151-162 MB)
-    large = {}
-    for name in ("collapse_2048x1024", "laplace_batch"):
-        lspecs = inputs.WORKLOADS[name]()
-        lnodes = sum(s.nodes for s in lspecs)
-        bl = lbm.Batch(lspecs, "fp32_dev", stream=stream)
-        bl.init()
-        # the shape for this workload: the fastest of a few on flushed steps
-        lt_ms = {}
-        for t in dict.fromkeys((best_tile, 1, 3, 5)):
-            lbm.lbm_set_tile(bl.ctx, t)
-            timed_steps(torch, bl.ctx, lbm, stream, flush, 3)
-            lt_ms[t] = statistics.mean(timed_steps(torch, bl.ctx, lbm, stream, flush, 15))
-        lt = min(lt_ms, key=lt_ms.get)
-        lbm.lbm_set_tile(bl.ctx, lt)
-        lms = statistics.mean(timed_steps(torch, bl.ctx, lbm, stream, flush, 40))
-        lgbs = ALG_BYTES_FP32 * lnodes / (lms * 1e-3) / 1e9
-        large[name] = {"nodes": lnodes, "tile": lbm.lbm_tile_shape(lt), "tile_index": lt, "ms_per_step": lms,
-                       "MLUPS": lnodes / (lms * 1e-3) / 1e6, "achieved_gbs": lgbs}
-        bl.close()
-
-    peak, peak_kind = measured_peak_hbm()
-    for v in large.values():
-        v["frac"] = v["achieved_gbs"] / peak
     achieved = ALG_BYTES_FP32 * nodes / (ms_per_step * 1e-3) / 1e9
-    kinds = {lbm.LBM_TILE_PLAIN: "plain", lbm.LBM_TILE_PIPELINED: "pipelined"}
     traffic = profiled_traffic(best_tile, kinds.get(lbm.lbm_tile_kind(best_tile)))
 
     line = {
@@ -438,9 +515,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_node": ALG_BYTES_FP32},
+        "sustained": dict(sustained, note="back-to-back steps, CUDA-graph replay of 256 steps, events around "
+                                          "the replay, no flush; working sets larger than L2 (129 MB)"),
         "copy_same_bytes": {"achieved_gbs": copy_gbs, "ms": copy_ms, "frac": copy_gbs / peak,
                             "note": "torch device copy of 9 x 4 B per node, same flush"},
-        "large_workloads": large,
         "fp32_vs_fp64": acc,
         "fp64_plain": {"value": fp64_mlups, "unit": "MLUPS", "ms_per_step": fp64_ms, "steps": k64,
                        "achieved_gbs": ALG_BYTES_FP64 * nodes / (fp64_ms * 1e-3) / 1e9},
@@ -453,11 +531,16 @@ def main():
         "clocks": clk,
         "wall_s_timed_loop": t_wall,
     }
+    if sharded is not None:
+        line["sharded"] = sharded
     if rank == 0 and world == 1:
-        cpu_mlups, cpu_steps, cpu_s = time_oracle(specs, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": cpu_mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        cores = host_cores()
+        cpu_mlups, cpu_steps, cpu_s, used = time_oracle(specs, args.cpu_seconds, threads=cores)
+        one_mlups, one_steps, one_s, _ = time_oracle(specs, max(2.0, args.cpu_seconds / 4), threads=1)
+        line["cpu_baseline"] = {"value": cpu_mlups, "unit": "MLUPS", "cores": used, "kind": "oracle",
                                 "sample": f"{cpu_steps} whole time steps of all {len(specs)} lattices "
-                                          f"({cpu_s:.1f} s, single thread)"}
+                                          f"({cpu_s:.1f} s, {used} threads, OpenMP over the nodes)",
+                                "single_thread": {"value": one_mlups, "steps": one_steps, "seconds": one_s}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -58,6 +58,8 @@ def _load():
         lib.oracle_moments.restype = ctypes.c_uint
         lib.oracle_mass.argtypes = [P, _dp]
         lib.oracle_mass.restype = ctypes.c_double
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_openmp.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -143,6 +145,15 @@ class Lattice:
         self.lib.oracle_collide_node(ctypes.byref(self.p), _ptr(f), float(Fx), float(Fy),
                                      float(psi), float(g2), _ptr(out))
         return out
+
+
+def set_threads(n: int) -> bool:
+    """Run the sweeps of every lattice's step on n threads (1: serial, the
+    default). Returns False if the oracle was built without OpenMP (then it
+    stays serial). Results are bitwise the same for any n."""
+    lib = _load()
+    lib.oracle_set_threads(int(n))
+    return bool(lib.oracle_openmp())
 
 
 def moment_matrix():

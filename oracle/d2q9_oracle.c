@@ -37,6 +37,11 @@
  *    where F = -G psi g.
  *
  * Array layout: f[a][y][x], a = 0..8, x fastest, nx*ny nodes per plane.
+ *
+ * Threads: the three sweeps update every node from read-only inputs and
+ * write disjoint outputs, so they may run their node loops on several
+ * threads (OpenMP, oracle_set_threads; one thread unless asked) with
+ * bitwise the same result. The mass sum stays serial, in node order.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -53,6 +58,19 @@ static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static const double WINT[Q] = {0.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0,
                                1.0 / 12.0, 1.0 / 12.0, 1.0 / 12.0, 1.0 / 12.0};
 static const double CS2 = 1.0 / 3.0;
+
+/* Threads of the sweeps' node loops (1: serial). */
+static int g_threads = 1;
+
+void oracle_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+
+int oracle_openmp(void) {
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 /* Flags returned by the oracle. */
 #define OR_FLAG_PSI_CLAMPED 1u
@@ -343,6 +361,7 @@ static unsigned sweep_density_psi(const oracle_params* P, const double* f, doubl
                                   double* psi) {
     size_t N = (size_t)P->nx * P->ny;
     unsigned flag = 0;
+#pragma omp parallel for num_threads(g_threads) reduction(|:flag) schedule(static)
     for (size_t i = 0; i < N; ++i) {
         int x = (int)(i % P->nx), y = (int)(i / P->nx);
         if (is_solid(P, x, y)) {
@@ -363,7 +382,7 @@ static unsigned sweep_density_psi(const oracle_params* P, const double* f, doubl
 static void sweep_collide(const oracle_params* P, const double* f, const double* psi,
                           double* fstar) {
     size_t N = (size_t)P->nx * P->ny;
-    double fn[Q], fs[Q];
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int y = 0; y < P->ny; ++y)
         for (int x = 0; x < P->nx; ++x) {
             size_t i = (size_t)y * P->nx + x;
@@ -371,6 +390,7 @@ static void sweep_collide(const oracle_params* P, const double* f, const double*
                 for (int a = 0; a < Q; ++a) fstar[(size_t)a * N + i] = f[(size_t)a * N + i];
                 continue;
             }
+            double fn[Q], fs[Q];
             double Fx, Fy, g2;
             force_at(P, psi, x, y, &Fx, &Fy, &g2);
             for (int a = 0; a < Q; ++a) fn[a] = f[(size_t)a * N + i];
@@ -383,6 +403,10 @@ static void sweep_collide(const oracle_params* P, const double* f, const double*
  * reflected back into the node it left, as the opposite population. */
 static void sweep_stream(const oracle_params* P, const double* fstar, double* f) {
     size_t N = (size_t)P->nx * P->ny;
+    /* each f_a(x) of a fluid node is written once: by the fluid node x - e_a
+     * streaming into x, or, when x - e_a is solid, by x's own reflection; a
+     * solid node writes only its own values */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int y = 0; y < P->ny; ++y)
         for (int x = 0; x < P->nx; ++x) {
             size_t i = (size_t)y * P->nx + x;

@@ -25,6 +25,9 @@ Workloads (all a = 1, b = 4, R = 1, G = -1, c_s^2 = 1/3):
   collapse_2048x1024  2048x1024, solid rows y = 0 and y = 1023, periodic in x,
                       vapour bubble R0 = 200 at (1023.5, 300) in liquid at
                       1.05 x rho_l, W = 5, T = 0.5 Tc, tau_nu = 0.6, eps = 1.86
+  roofline_4096       4096^2 periodic with the physics of cavitation_1024
+                      (1.2 GB of distributions, ten times the L2)
+  collapse_x8         eight collapse_2048x1024 lattices in one batch (1.2 GB)
 """
 import json
 import math
@@ -188,6 +191,16 @@ def cavitation_1024(n: int = 1024, config_id: int = 3) -> List[LatticeSpec]:
                         meta={"rho0": rho0, "rho_c": coexistence_table()["rho_c"]})]
 
 
+def roofline_4096(n: int = 4096, config_id: int = 9) -> List[LatticeSpec]:
+    """The cavitation workload's physics on a 4096^2 lattice: a working set
+    far larger than L2, for the sustained-bandwidth measurement."""
+    return cavitation_1024(n, config_id)
+
+
+def collapse_x8() -> List[LatticeSpec]:
+    return collapse() * 8
+
+
 def collapse(nx: int = 2048, ny: int = 1024, R0: float = 200.0, yc: float = 300.0) -> List[LatticeSpec]:
     Tc = critical_temperature()
     c = coexistence(0.5)
@@ -207,4 +220,6 @@ WORKLOADS = {
     "laplace_batch": laplace_batch,
     "cavitation_1024": cavitation_1024,
     "collapse_2048x1024": collapse,
+    "roofline_4096": roofline_4096,
+    "collapse_x8": collapse_x8,
 }

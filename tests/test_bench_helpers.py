@@ -65,12 +65,20 @@ def _sampler(monkeypatch, lines):
 
 
 def test_clock_samples_are_summarised(monkeypatch):
-    row = "0, {sm}, 2070, 900.5, {act}, Not Active, Not Active, Not Active, {cap}"
-    lines = [row.format(sm=s, act="0x0", cap="Not Active") for s in (2070, 2070, 2055)]
-    lines.append(row.format(sm=1980, act="0x4", cap="Active"))
+    row = "0, {sm}, 2070, 900.5, {act}, Not Active, Not Active, Not Active, {cap}, {util}"
+    lines = [row.format(sm=s, act="0x0", cap="Not Active", util=u) for s, u in ((2070, 97), (2070, 88), (2055, 91))]
+    lines.append(row.format(sm=1980, act="0x4", cap="Active", util=99))
+    lines.append(row.format(sm=345, act="0x0", cap="Not Active", util=0))   # idle: not under load
     lines.append("garbage line")
     clk = _sampler(monkeypatch, lines).stop()
-    assert clk == {"sm_mhz": 2062.5, "sm_max_mhz": 2070.0, "samples": 4, "reasons": ["sw_power_cap"]}
+    assert clk == {"sm_mhz": 2062.5, "sm_max_mhz": 2070.0, "samples": 5, "samples_under_load": 4,
+                   "reasons": ["sw_power_cap"]}
+
+
+def test_clock_median_falls_back_to_all_samples_without_utilisation(monkeypatch):
+    lines = ["0, %d, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active" % s for s in (2070, 2000, 2055)]
+    clk = _sampler(monkeypatch, lines).stop()
+    assert clk["sm_mhz"] == 2055 and clk["samples_under_load"] == 0
 
 
 def test_thermal_and_hardware_slowdowns_are_reported(monkeypatch):

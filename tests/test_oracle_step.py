@@ -360,3 +360,17 @@ def test_readout_velocity_vanishes_at_steady_flat_interface(tr, eps):
     assert np.abs(jx / rho).max() > 0.05
     assert np.abs(ux).max() < 1e-9
     assert np.abs(uy).max() < 1e-15
+
+
+def test_threaded_sweeps_are_bitwise_serial():
+    # The sweeps update nodes independently, so running them on several
+    # threads gives the serial result bit for bit (walls included).
+    runs = []
+    for n in (1, 4):
+        if not d2q9.set_threads(n) and n > 1:
+            pytest.skip("oracle built without OpenMP")
+        L = _droplet_lattice(45, 37, 0.7, 1.86, 0.6, walls=True)
+        L.step(30)
+        runs.append((L.f.copy(), L.flags))
+    d2q9.set_threads(1)
+    assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
