@@ -2,9 +2,12 @@
 
 - ``bubble_batch``: static vapour bubbles (Eq. 16 with vapour inside) of several
   radii on periodic square lattices, one batch.
-- ``laplace_fit``: runs a batch through the C ABI and fits the Laplace law,
-  Eq. 17, |p_out - p_in| = sigma / r, with r the equivalent radius of the
-  vapour area and p of Eq. 10 averaged inside the bubble and in the far liquid.
+- ``laplace_fit`` / ``laplace_series``: run a batch of bubbles (or droplets)
+  through the C ABI and fit the Laplace law, Eq. 17, |p_out - p_in| = sigma / r,
+  with r the equivalent radius of the inner phase's area and p of Eq. 10
+  averaged in the inner half of the bubble and in the far outer phase.
+- ``vapour_fraction_history``: phi(t), the fraction of nodes below the
+  critical density, for the homogeneous cavitation workload.
 
 Eq. 17 is printed as p_out - p_in = sigma / r; a bubble's inside pressure is
 the higher one, so the fit uses the magnitude. The coexistence densities the
@@ -48,26 +51,17 @@ def measure_bubbles(batch: "lbm.Batch") -> List[dict]:
 
         def mean(a, sel):
             return float(a[sel].mean()) if sel.any() else float("nan")   # nan: a run that diverged
-        out.append({"R0": s.meta["R0"], "r": r_eq, "rho_in": mean(rho, inner), "rho_out": mean(rho, outer),
+        out.append({"R0": s.meta.get("R0", s.meta.get("R")), "r": r_eq, "rho_in": mean(rho, inner), "rho_out": mean(rho, outer),
                     "p_in": mean(p, inner), "p_out": mean(p, outer),
                     "umax": float(max(np.abs(ux).max(), np.abs(uy).max())), "status": batch.status(i)})
     return out
 
 
-def laplace_fit(radii: Sequence[float], t_over_tc: float, steps: int, a: float = 1.0, tau_nu: float = 0.6,
-                eps: float = 1.86, n: int = 201, stream=None, precision: str = "fp32_dev") -> dict:
-    """Run static bubbles for `steps` steps and fit the Laplace law.
-
-    `sigma` is the least-squares slope of Eq. 17 as written, |dp| = sigma / r
-    (a line through the origin); `sigma_free`, `intercept` and `r2` are the
-    fit |dp| = sigma / r + c, whose small intercept and r2 near 1 show that
-    the bubbles obey the 1/r law."""
-    specs = bubble_batch(radii, t_over_tc, a=a, n=n, tau_nu=tau_nu, eps=eps)
-    b = lbm.Batch(specs, precision, stream=stream)
-    b.init()
-    b.step(steps)
-    rows = measure_bubbles(b)
-    b.close()
+def fit_laplace(rows: Sequence[dict]) -> dict:
+    """Fit Eq. 17 to measured bubbles or droplets: `sigma` is the
+    least-squares slope of |dp| = sigma / r (a line through the origin);
+    `sigma_free`, `intercept` and `r2` are the fit |dp| = sigma / r + c, whose
+    small intercept and r2 near 1 show that the series obeys the 1/r law."""
     inv_r = np.array([1.0 / r["r"] for r in rows])
     dp = np.array([abs(r["p_out"] - r["p_in"]) for r in rows])
     sigma = float(np.dot(inv_r, dp) / np.dot(inv_r, inv_r))
@@ -76,7 +70,72 @@ def laplace_fit(radii: Sequence[float], t_over_tc: float, steps: int, a: float =
     pred = A @ np.array([sigma_free, intercept])
     r2 = 1.0 - float(np.sum((dp - pred) ** 2) / np.sum((dp - dp.mean()) ** 2))
     return {"sigma": sigma, "sigma_free": float(sigma_free), "intercept": float(intercept), "r2": r2,
-            "bubbles": rows}
+            "bubbles": list(rows)}
+
+
+def laplace_series(specs: Sequence[inputs.LatticeSpec], steps: int, precision: str = "fp32_dev",
+                   stream=None, window: int = 0, every: int = 50) -> dict:
+    """Run static bubbles or droplets (one batch) for `steps` steps, measure
+    each (``measure_bubbles``: the inner phase is the one at the centre) and
+    fit the Laplace law (``fit_laplace``). With `window` > 0 the radius and
+    the two pressures are averaged over samples taken every `every` steps in
+    the last `window` steps, which removes the acoustic oscillation that a
+    large drop or bubble still carries when it has not yet decayed."""
+    b = lbm.Batch(list(specs), precision, stream=stream)
+    b.init()
+    b.step(steps - window)
+    samples = [measure_bubbles(b)]
+    done = steps - window
+    while done < steps:
+        k = min(every, steps - done)
+        b.step(k)
+        done += k
+        samples.append(measure_bubbles(b))
+    b.close()
+    rows = []
+    for i, r0 in enumerate(samples[0]):
+        row = dict(r0)
+        for key in ("r", "rho_in", "rho_out", "p_in", "p_out"):
+            row[key] = float(np.mean([smp[i][key] for smp in samples]))
+        row["umax"] = max(smp[i]["umax"] for smp in samples)
+        row["status"] = samples[-1][i]["status"]
+        rows.append(row)
+    return fit_laplace(rows)
+
+
+def laplace_fit(radii: Sequence[float], t_over_tc: float, steps: int, a: float = 1.0, tau_nu: float = 0.6,
+                eps: float = 1.86, n: int = 201, stream=None, precision: str = "fp32_dev") -> dict:
+    """Static bubbles of the given radii (``bubble_batch``) run for `steps`
+    steps, and the Laplace fit of ``fit_laplace``."""
+    specs = bubble_batch(radii, t_over_tc, a=a, n=n, tau_nu=tau_nu, eps=eps)
+    return laplace_series(specs, steps, precision=precision, stream=stream)
+
+
+def vapour_fraction(rho: np.ndarray, rho_c: float) -> float:
+    """Fraction of the nodes whose density is below the critical density."""
+    return float(np.count_nonzero(rho < rho_c)) / rho.size
+
+
+def vapour_fraction_history(spec: inputs.LatticeSpec, steps: int, every: int, precision: str = "fp32_dev",
+                            stream=None) -> dict:
+    """phi(t), the vapour fraction of a lattice every `every` steps."""
+    rho_c = inputs.coexistence_table()["rho_c"]
+    b = lbm.Batch([spec], precision, stream=stream)
+    b.init()
+    t, phi = [], []
+    done = 0
+    while True:
+        rho = b.moments(0, allow_flags=True)[0]
+        t.append(done)
+        phi.append(vapour_fraction(rho, rho_c))
+        if done >= steps:
+            break
+        k = min(every, steps - done)
+        b.step(k)
+        done += k
+    status = b.status(0)
+    b.close()
+    return {"t": t, "phi": phi, "status": status}
 
 
 def coexistence_curve(t_over_tc: Sequence[float], eps: Sequence[float], tau_nu: Sequence[float], steps: int,
