@@ -261,15 +261,15 @@ int lbm_get_state_view(lbm_ctx* ctx, int lat, lbm_state_view* view);
 
 /* Mass of one FP32-stored lattice without allocating any memory (the paper
  * has no counterpart: this serves callers that cannot allocate device memory
- * when they need the check, such as code running during CUDA-graph capture,
- * applications whose own allocator owns all device memory, or loops that must
- * not wait in the driver's allocator).
+ * when they need the check, such as applications whose own allocator owns all
+ * device memory, or loops that must not wait in the driver's allocator).
  *   f_dev      device pointer to the lattice's nine FP32 planes in the
  *              library's layout: plane a at f_dev + a*ny*pitch, node (x, y) at
  *              y*pitch + x, pitch = round_up(nx, 32) (the layout of a
  *              lbm_save_state blob's distribution section).
- *   nx, ny     lattice size, 1 <= ny <= LBM_NOALLOC_MAX_NY; larger sizes are
- *              rejected with LBM_EINVAL.
+ *   nx, ny     lattice size, 1 <= ny <= LBM_NOALLOC_MAX_NY and
+ *              9 * ny * round_up(nx, 32) < 2^31; other sizes are rejected with
+ *              LBM_EINVAL.
  *   rho_ref    the deviation reference the values are stored against (0 for
  *              plain FP32 storage).
  *   mask_dev   NULL, or ny*pitch device bytes, nonzero = solid (not counted).
@@ -281,10 +281,14 @@ int lbm_get_state_view(lbm_ctx* ctx, int lat, lbm_state_view* view);
  * The partial sums live in one fixed device array of LBM_NOALLOC_MAX_NY/8
  * doubles (32 KiB) that every device which loads the library holds until the
  * process exits; no cudaMalloc, cudaFree or allocating library call is made.
- * The first call on each device looks that array's device address up
+ * The first call on each device (and again under each new CUDA context, e.g.
+ * after cudaDeviceReset) looks that array's device address up
  * (cudaGetSymbolAddress) with the device current; make that first call
- * outside any stream capture. All calls share the array: calls whose work may
- * overlap on the GPU (different streams without ordering) race on it. */
+ * before any stream capture. All calls share the array: calls whose work may
+ * overlap on the GPU (different streams without ordering) race on it.
+ * Errors: LBM_EINVAL for null pointers or sizes out of range; LBM_ECUDA, with
+ * the CUDA error named, when a launch fails or when an error left by earlier
+ * CUDA work is pending (that error is left in place, not cleared). */
 int lbm_total_mass_fp32_noalloc(const float* f_dev, int nx, int ny, double rho_ref,
                                 const uint8_t* mask_dev, double* mass_dev, void* cuda_stream);
 

@@ -2,13 +2,15 @@
 // a fixed file-scope device array instead of memory obtained from cudaMalloc.
 //
 // Some callers cannot allocate device memory at the point where they want a
-// mass check: code running while a CUDA graph is being captured (an
-// allocation would break the capture), allocators that own all device memory
-// and hand out none, or real-time loops that must not stall in the driver's
+// mass check: applications whose own allocator owns all device memory and
+// hands out none, or real-time loops that must not stall in the driver's
 // allocator. This entry point serves them; it needs only the distribution
 // they already hold and an 8-byte output.
+#include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -30,9 +32,40 @@ constexpr int kMaxPartials = LBM_NOALLOC_MAX_NY / kRowsPerBlock;
 // race on it.
 static __device__ __align__(256) double g_partials[kMaxPartials];
 
+// The array's device address is looked up once per device and CUDA context
+// (cudaGetSymbolAddress, with that device current) and kept with the context
+// it belongs to: a call under another context (a primary context created
+// anew after cudaDeviceReset, or a context the caller made current) looks it
+// up again instead of using an address of another context.
 constexpr int kMaxDevices = 64;
+struct ScratchAddr {
+    CUcontext ctx;
+    double* addr;
+};
 std::mutex g_mutex;
-double* g_partials_addr[kMaxDevices] = {};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+// The calling thread's current context, through the driver entry point (the
+// library does not link the driver library itself); null if none is current.
+CUcontext current_context() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    if (fn == nullptr) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || p == nullptr)
+            return nullptr;
+        fn = (PFN_cuCtxGetCurrent_v4000)p;
+    }
+    CUcontext c = nullptr;
+    return fn(&c) == CUDA_SUCCESS ? c : nullptr;
+}
+
+int cuda_error(const char* what, cudaError_t e) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "lbm_total_mass_fp32_noalloc: %s: %s", what, cudaGetErrorString(e));
+    return lbm::report_error(LBM_ECUDA, msg);
+}
 
 // Block b sums, over the fluid nodes of rows [8b, 8b + 8), rho_ref + the nine
 // stored values, in a fixed order (threads stride the rows, then a fixed tree).
@@ -84,34 +117,39 @@ extern "C" int lbm_total_mass_fp32_noalloc(const float* f_dev, int nx, int ny, d
     if (9 * (long long)ny * pitch >= (1LL << 31))
         return lbm::report_error(LBM_EINVAL, "lbm_total_mass_fp32_noalloc: lattice too large (9*ny*pitch >= 2^31)");
 
+    // An error left by earlier asynchronous work is reported as such and left
+    // in place (peeked, not cleared), so the caller still sees its own state.
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) return cuda_error("an error from earlier CUDA work is pending", pending);
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return lbm::report_error(LBM_ECUDA, "lbm_total_mass_fp32_noalloc: no usable current device");
-    }
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error("no usable current device", e);
+    if (dev < 0 || dev >= kMaxDevices)
+        return lbm::report_error(LBM_ECUDA, "lbm_total_mass_fp32_noalloc: device ordinal beyond 63");
     double* partials = nullptr;
     {
-        // Set-up once per device, with that device current: the host-side name
-        // g_partials is not a device address, so ask the runtime for it.
+        // Set-up once per device and context, with that device current: the
+        // host-side name g_partials is not a device address, so ask the
+        // runtime for it (this also creates the primary context if none is
+        // current yet, hence the context is read again afterwards).
         std::lock_guard<std::mutex> lock(g_mutex);
-        if (g_partials_addr[dev] == nullptr) {
+        CUcontext ctx = current_context();
+        if (ctx == nullptr || g_scratch[dev].ctx != ctx || g_scratch[dev].addr == nullptr) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || p == nullptr) {
-                cudaGetLastError();
-                return lbm::report_error(LBM_ECUDA, "lbm_total_mass_fp32_noalloc: cudaGetSymbolAddress failed");
-            }
-            g_partials_addr[dev] = (double*)p;
+            e = cudaGetSymbolAddress(&p, g_partials);
+            if (e != cudaSuccess || p == nullptr) return cuda_error("cudaGetSymbolAddress failed", e);
+            g_scratch[dev] = ScratchAddr{current_context(), (double*)p};
         }
-        partials = g_partials_addr[dev];
+        partials = g_scratch[dev].addr;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int blocks = (ny + kRowsPerBlock - 1) / kRowsPerBlock;
     noalloc_mass_partial<<<blocks, kThreads, 0, s>>>(f_dev, nx, ny, (int)pitch, rho_ref, mask_dev,
                                                      partials);
-    if (cudaGetLastError() != cudaSuccess)
-        return lbm::report_error(LBM_ECUDA, "lbm_total_mass_fp32_noalloc: partial-sum launch failed");
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_error("partial-sum launch failed", e);
     noalloc_mass_final<<<1, 1, 0, s>>>(partials, blocks, mass_dev);
-    if (cudaGetLastError() != cudaSuccess)
-        return lbm::report_error(LBM_ECUDA, "lbm_total_mass_fp32_noalloc: final-sum launch failed");
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_error("final-sum launch failed", e);
     return LBM_OK;
 }

@@ -1,8 +1,8 @@
 """The mass entry point that allocates nothing, against the context's own.
 
 lbm_total_mass_fp32_noalloc serves callers that cannot allocate device memory
-when they need a mass check (during CUDA-graph capture, under an allocator
-that owns all device memory, in loops that must not wait on the allocator).
+when they need a mass check (under an allocator that owns all device memory,
+in loops that must not wait on the allocator).
 It takes the FP32 distribution by device pointer; here that distribution is
 the one a context holds, taken from its checkpoint blob, and its result must
 equal lbm_total_mass on the same state. The file is collected last so that a
