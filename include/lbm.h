@@ -256,6 +256,57 @@ int lbm_info(lbm_ctx* ctx, lbm_info_t* info);
  * argument or a lattice index out of range. No device work, no sync. */
 int lbm_get_state_view(lbm_ctx* ctx, int lat, lbm_state_view* view);
 
+/* ---- one lattice split into x-slabs (one context or rank per slab) ------
+ * The scheme's step reads, at a node, its neighbours' state up to two
+ * columns away (the pull of Eq. 5 reaches one column, and the psi of Eq. 13
+ * on the one-cell ring around a node's neighbours needs their pulled
+ * density, which reaches the next). A lattice split at x cuts into slabs
+ * therefore exchanges, per face and step, LBM_HALO_ROWS = 12 values per row:
+ * the nine populations of the edge column (the neighbour's halo node there
+ * pulls those that point across the cut or along it, and reads the others
+ * back where a link comes from a solid cell), and the three of the next
+ * column that point across the cut.
+ *
+ * Mark lattice `lat` as one such slab: its x edges are no longer periodic;
+ * the pulls across them read the frame columns x = -2, -1 (left neighbour)
+ * and nx, nx + 1 (right neighbour) of the state, which lbm_halo_unpack
+ * fills. Rows stay periodic (and may carry walls). Call before
+ * lbm_init_fields; nx >= 2; with LBM_FP32_DEV the lattice's rho_ref must be
+ * given (>= 0) and equal in every slab of the lattice, so that the stored
+ * deviations they exchange mean the same.
+ *   halo_mask  NULL, or 4*ny bytes: the wall mask of columns -2, -1, nx and
+ *              nx + 1 (ny rows each, in that order), i.e. the neighbouring
+ *              slabs' edge columns. NULL takes each edge column of the
+ *              lattice's own mask as continuing across the cut. Must be
+ *              NULL or clear for a lattice without a wall mask.
+ * Afterwards, for this lattice:
+ *   - lbm_init_fields takes (nx + 2) x ny arrays (x = -1 .. nx, x fastest):
+ *     the slab's own field with the neighbouring slabs' edge columns on
+ *     either side; it also fills the frame, so the first step needs no
+ *     exchange. lbm_init_fields_all is refused for such a context.
+ *   - lbm_step(ctx, n) takes n <= 1: exchange the halos between steps.
+ *   - the read-outs (lbm_read_moments*) pull across the cut too: exchange
+ *     after the last step before reading.
+ *   - a checkpoint holds the slab's own nodes; exchange after a load. */
+#define LBM_HALO_ROWS 12
+int lbm_set_open_x(lbm_ctx* ctx, int lat, const uint8_t* halo_mask);
+
+/* Halo exchange of a slab (asynchronous on the context's stream; device
+ * buffers of LBM_HALO_ROWS*ny elements of the storage type: 4-byte floats
+ * for the FP32 precisions, 8-byte doubles for LBM_FP64; rows k*ny .. k*ny +
+ * ny - 1 hold value k of every row y).
+ *   lbm_halo_pack    writes into dev_out what the neighbour on `side`
+ *                    (0: left, x < 0; 1: right, x >= nx) pulls from this
+ *                    slab's current state.
+ *   lbm_halo_unpack  writes the halo packed by the neighbour on `side` (its
+ *                    pack of the opposite side) into this slab's frame.
+ * The transport between the two (NCCL send/recv, a peer copy, a host copy)
+ * is the caller's; order it with the context's stream. Per step: step, pack
+ * both sides, exchange, unpack both sides. LBM_EINVAL for a lattice not
+ * open in x, a side other than 0 or 1, or a null buffer. */
+int lbm_halo_pack(lbm_ctx* ctx, int lat, int side, void* dev_out);
+int lbm_halo_unpack(lbm_ctx* ctx, int lat, int side, const void* dev_in);
+
 /* Largest ny accepted by lbm_total_mass_fp32_noalloc. */
 #define LBM_NOALLOC_MAX_NY 32768
 

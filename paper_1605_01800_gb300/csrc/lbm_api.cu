@@ -62,6 +62,7 @@ struct HostLattice {
     bool rho_ref_auto;
     long long n_fluid;
     long long c_off;             // element offset in the compact checkpoint layout
+    std::vector<uint8_t> halo_mask;  // open in x: mask columns -2, -1, nx, nx + 1 (ny each)
 };
 
 }  // namespace
@@ -358,7 +359,7 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         // whose cells and two-cell frame hold none takes the wall-free paths
         const int ex = g.nx + 4, ey = g.ny + 4;
         std::vector<int> sat;
-        if (g.has_mask) {
+        if (geom_mask(g)) {
             sat.assign((size_t)(ex + 1) * (ey + 1), 0);
             for (int j = 0; j < ey; ++j)
                 for (int i = 0; i < ex; ++i) {
@@ -372,13 +373,16 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         for (int y0 = 0; y0 < g.ny; y0 += ty)
             for (int x0 = 0; x0 < g.nx; x0 += tx) {
                 const bool full = x0 + tx <= g.nx && y0 + ty <= g.ny;
-                bool clear = !g.has_mask;
-                if (g.has_mask && full) {  // frame [x0 - 2, x0 + tx + 2) x [y0 - 2, y0 + ty + 2)
+                bool clear = !geom_mask(g);
+                if (geom_mask(g) && full) {  // frame [x0 - 2, x0 + tx + 2) x [y0 - 2, y0 + ty + 2)
                     const int i0 = x0, i1 = x0 + tx + 4, j0 = y0, j1 = y0 + ty + 4;
                     const int n = sat[(size_t)j1 * (ex + 1) + i1] - sat[(size_t)j0 * (ex + 1) + i1] -
                                   sat[(size_t)j1 * (ex + 1) + i0] + sat[(size_t)j0 * (ex + 1) + i0];
                     clear = n == 0;
                 }
+                // an x-slab's tiles within two cells of its x edges pull from
+                // the frame (the halo): the general path, which does not wrap
+                if (geom_open_x(g) && (x0 < 2 || x0 + tx > g.nx - 2)) clear = false;
                 // no pull of the tile or of its halo ring crosses an edge
                 const bool inner = x0 >= 2 && x0 + tx <= g.nx - 2 && y0 >= 2 && y0 + ty <= g.ny - 2;
                 if (pipe && clear && full && g.nx >= 4 && g.ny >= 4 && L.desc.eos.kind == LBM_EOS_CS)
@@ -478,6 +482,36 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     drop_graphs(c);
     if (is_tma(tile_index)) return build_tma(c, tile_index);
     return LBM_OK;
+}
+
+// The mask plane of lattice l: its nodes, and in the frame their periodic
+// images, or for a lattice open in x the halo mask columns x = -2, -1, nx,
+// nx + 1 (rows wrap periodically in both cases).
+cudaError_t upload_mask(lbm_ctx* c, int l) {
+    const HostLattice& L = c->lats[l];
+    if (L.mask.empty()) return cudaSuccess;
+    const Geom& g = L.geom;
+    std::vector<uint8_t> rows((size_t)g.plane, 0);
+    for (int y = -kGY; y < g.ny + kGY; ++y)
+        for (int x = -2; x < g.nx + 2; ++x) {
+            const int ys = (int)(((long long)y % g.ny + g.ny) % g.ny);
+            uint8_t v;
+            if (geom_open_x(g) && (x < 0 || x >= g.nx)) {
+                const int col = x < 0 ? x + 2 : x - g.nx + 2;  // -2, -1, nx, nx + 1 -> 0 .. 3
+                v = L.halo_mask[(size_t)col * g.ny + ys];
+            } else {
+                const int xs = (int)(((long long)x % g.nx + g.nx) % g.nx);
+                v = L.mask[(size_t)ys * g.nx + xs];
+            }
+            rows[(size_t)node_index(g, x, y)] = v;
+        }
+    return cudaMemcpy(c->d_mask + g.mask_off, rows.data(), rows.size(), cudaMemcpyHostToDevice);
+}
+
+bool any_open_x(const lbm_ctx* c) {
+    for (const auto& L : c->lats)
+        if (geom_open_x(L.geom)) return true;
+    return false;
 }
 
 int upload_phys(lbm_ctx* c) {
@@ -683,6 +717,44 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
     return LBM_OK;
 }
 
+// Initial state of lattice `lat`, open in x, from host arrays of
+// (nx + 2) x ny values (the neighbouring slabs' edge columns included),
+// through a temporary device buffer.
+int init_open(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy) {
+    HostLattice& L = c->lats[lat];
+    const Geom& g = L.geom;
+    const size_t n = (size_t)(g.nx + 2) * g.ny;
+    const int nf = 1 + (ux ? 1 : 0) + (uy ? 1 : 0);
+    double* d = nullptr;
+    int rc = dev_alloc(c, &d, (size_t)nf * n * sizeof(double));
+    if (rc) return rc;
+    double* d_rho = d;
+    double* d_ux = ux ? d + n : nullptr;
+    double* d_uy = uy ? d + (ux ? 2 : 1) * n : nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_rho, rho, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && ux) e = cudaMemcpyAsync(d_ux, ux, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && uy) e = cudaMemcpyAsync(d_uy, uy, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (++c->bad_gen == 0) c->bad_gen = 1;
+    if (e == cudaSuccess) {
+        if (c->precision == LBM_FP64)
+            e = launch_init_open_f64(g, L.rho_ref, d_rho, d_ux, d_uy, c->d_mask, (double*)c->f[c->cur], c->m_bad,
+                                     lat, c->bad_gen, c->stream);
+        else
+            e = launch_init_open_f32(g, L.rho_ref, d_rho, d_ux, d_uy, c->d_mask, (float*)c->f[c->cur], c->m_bad,
+                                     lat, c->bad_gen, c->stream);
+        if (e == cudaSuccess) c->launches += 1;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    c->device_bytes -= (size_t)nf * n * sizeof(double);
+    if (e != cudaSuccess) return cuda_fail(e, "open-lattice init");
+    if (c->h_bad[lat] == c->bad_gen)
+        return fail(LBM_EINVAL,
+                    "lattice %d: a fluid density is not finite and > 0, or a velocity is not finite "
+                    "(the lattice's state is undefined until the next successful init)", lat);
+    return LBM_OK;
+}
+
 // rho, v, p of lattices [lat0, lat0 + n_lat) into host arrays that start at
 // lattice lat0's first node: one kernel launch, one download per field.
 int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, double* uy, double* p) {
@@ -763,11 +835,11 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
             for (auto& b : L.mask) b = b ? 1 : 0;
             L.n_fluid = 0;
             for (auto b : L.mask) L.n_fluid += (b == 0);
-            g.has_mask = 1;
+            g.flags = kGeomMask;
             g.mask_off = m_off;
             m_off += round_up(g.plane, 256);
         } else {
-            g.has_mask = 0;
+            g.flags = 0;
             g.mask_off = 0;
         }
         // keep each lattice's planes 256-byte aligned
@@ -824,21 +896,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, n * sizeof(unsigned));
     if (e == cudaSuccess && m_off > 0) {
         e = cudaMemset(c->d_mask, 0, (size_t)m_off);
-        std::vector<uint8_t> rows;
-        for (int i = 0; i < n && e == cudaSuccess; ++i) {
-            const HostLattice& L = c->lats[i];
-            if (L.mask.empty()) continue;
-            const Geom& g = L.geom;
-            // the nodes, and their periodic images in the frame (no pull reads them)
-            rows.assign((size_t)g.plane, 0);
-            for (int y = -kGY; y < g.ny + kGY; ++y)
-                for (int x = -2; x < g.nx + 2; ++x) {
-                    const int xs = (int)(((long long)x % g.nx + g.nx) % g.nx);
-                    const int ys = (int)(((long long)y % g.ny + g.ny) % g.ny);
-                    rows[(size_t)node_index(g, x, y)] = L.mask[(size_t)ys * g.nx + xs];
-                }
-            e = cudaMemcpy(c->d_mask + g.mask_off, rows.data(), rows.size(), cudaMemcpyHostToDevice);
-        }
+        for (int i = 0; i < n && e == cudaSuccess; ++i) e = upload_mask(c, i);
     }
     if (e == cudaSuccess) {
         std::vector<Geom> geoms(n);
@@ -899,7 +957,7 @@ int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, co
     int rc = check_lat(c, lat);
     if (rc) return rc;
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
-    rc = init_range(c, lat, 1, rho, ux, uy);
+    rc = geom_open_x(c->lats[lat].geom) ? init_open(c, lat, rho, ux, uy) : init_range(c, lat, 1, rho, ux, uy);
     if (rc) return rc;
     c->steps = 0;
     return LBM_OK;
@@ -909,6 +967,9 @@ int lbm_init_fields_all(lbm_ctx* c, const double* rho, const double* ux, const d
     Range range("lbm_init_fields_all");
     if (!c) return fail(LBM_EINVAL, "null context");
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
+    if (any_open_x(c))
+        return fail(LBM_EINVAL, "a lattice of this context is open in x: initialise it with lbm_init_fields "
+                                "((nx + 2) x ny arrays)");
     int rc = init_range(c, 0, c->n, rho, ux, uy);
     if (rc) return rc;
     c->steps = 0;
@@ -919,6 +980,9 @@ int lbm_step(lbm_ctx* c, int n) {
     Range range("lbm_step");
     if (!c) return fail(LBM_EINVAL, "null context");
     if (n < 0) return fail(LBM_EINVAL, "n=%d must be >= 0", n);
+    if (n > 1 && any_open_x(c))
+        return fail(LBM_EINVAL, "n=%d: a lattice open in x needs its halo exchanged between steps; step one "
+                                "at a time", n);
     int done = 0;
     if (capturable_stream(c->stream)) {
         while (n - done >= kGraphChunk) {
@@ -1260,6 +1324,72 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->n_tiles = c->n_tiles + c->n_fast + c->n_tma;
     info->graph_chunk = kGraphChunk;
     return LBM_OK;
+}
+
+int lbm_set_open_x(lbm_ctx* c, int lat, const uint8_t* halo_mask) {
+    Range range("lbm_set_open_x");
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    HostLattice& L = c->lats[lat];
+    Geom& g = L.geom;
+    if (g.nx < 2) return fail(LBM_EINVAL, "lattice %d: an x-slab needs nx >= 2 (nx=%d)", lat, g.nx);
+    if (c->precision == LBM_FP32_DEV && L.rho_ref_auto)
+        return fail(LBM_EINVAL, "lattice %d: an x-slab needs an explicit rho_ref (>= 0) shared by every slab of "
+                                "its lattice, so that their stored halos mean the same", lat);
+    if (L.mask.empty()) {
+        if (halo_mask)
+            for (long long i = 0; i < 4LL * g.ny; ++i)
+                if (halo_mask[i]) return fail(LBM_EINVAL, "lattice %d has no wall mask: halo_mask must be clear", lat);
+    } else {
+        L.halo_mask.assign((size_t)4 * g.ny, 0);
+        for (int col = 0; col < 4; ++col)
+            for (int y = 0; y < g.ny; ++y) {
+                const int xe = col < 2 ? 0 : g.nx - 1;  // the edge column continued across the cut
+                L.halo_mask[(size_t)col * g.ny + y] =
+                    halo_mask ? (halo_mask[(size_t)col * g.ny + y] ? 1 : 0) : L.mask[(size_t)y * g.nx + xe];
+            }
+    }
+    const int old_flags = g.flags;
+    g.flags |= kGeomOpenX;
+    cudaError_t e = upload_mask(c, lat);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_geom + lat, &g, sizeof(Geom), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        g.flags = old_flags;
+        cudaMemcpy(c->d_geom + lat, &g, sizeof(Geom), cudaMemcpyHostToDevice);
+        return cuda_fail(e, "x-slab set-up");
+    }
+    rc = build_tiles(c, c->tile_index);  // the tiles at the x edges now take the general path
+    if (rc) {
+        g.flags = old_flags;
+        cudaMemcpy(c->d_geom + lat, &g, sizeof(Geom), cudaMemcpyHostToDevice);
+        return rc;
+    }
+    return LBM_OK;
+}
+
+static int halo_call(lbm_ctx* c, int lat, int side, void* buf, bool pack) {
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    if (!geom_open_x(c->lats[lat].geom)) return fail(LBM_EINVAL, "lattice %d is not open in x (lbm_set_open_x)", lat);
+    if (side != 0 && side != 1) return fail(LBM_EINVAL, "side=%d must be 0 (left) or 1 (right)", side);
+    if (!buf) return fail(LBM_EINVAL, "null halo buffer");
+    const Geom& g = c->lats[lat].geom;
+    cudaError_t e = c->precision == LBM_FP64
+                        ? launch_halo_f64(g, (double*)c->f[c->cur], side, (double*)buf, pack, c->stream)
+                        : launch_halo_f32(g, (float*)c->f[c->cur], side, (float*)buf, pack, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, pack ? "halo pack" : "halo unpack");
+    c->launches += 1;
+    return LBM_OK;
+}
+
+int lbm_halo_pack(lbm_ctx* c, int lat, int side, void* dev_out) {
+    Range range("lbm_halo_pack");
+    return halo_call(c, lat, side, dev_out, true);
+}
+
+int lbm_halo_unpack(lbm_ctx* c, int lat, int side, const void* dev_in) {
+    Range range("lbm_halo_unpack");
+    return halo_call(c, lat, side, const_cast<void*>(dev_in), false);
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }

@@ -40,7 +40,7 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const double rho_ref = phys[lat].rho_ref;
-    const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
+    const uint8_t* mask = geom_mask(g) ? mask_base + g.mask_off : nullptr;
     T* f = f_base + g.f_off;
     rho += g.node_off;
     if (ux) ux += g.node_off;
@@ -75,6 +75,100 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
     if (invalid) bad[lat] = gen;
 }
 
+// Initial state of one x-slab (a lattice open in x): rho/ux/uy hold
+// (nx + 2) x ny values, column x + 1 for x = -1 .. nx (the neighbouring
+// slabs' edge columns on either side). As init_kernel, with the pulls across
+// the x edges taken from those columns instead of wrapping, and with the
+// frame columns the first step pulls from filled as well: x = -1 and x = nx
+// with every population (the halo ring's nodes there pull some, and read
+// others back where a link comes from a solid cell), x = -2 and x = nx + 1
+// with the populations pointing into the lattice. Frame entries no pull
+// reads are set to 0.
+template <typename T>
+__global__ void init_open_kernel(Geom g, double rho_ref, const double* __restrict__ rho,
+                                 const double* __restrict__ ux, const double* __restrict__ uy,
+                                 const uint8_t* __restrict__ mask_base, T* __restrict__ f_base,
+                                 unsigned* __restrict__ bad, int lat, unsigned gen) {
+    const uint8_t* mask = geom_mask(g) ? mask_base + g.mask_off : nullptr;
+    T* f = f_base + g.f_off;
+    const int w = g.nx + 2;                 // columns of the input arrays
+    const long long n = (long long)(g.nx + 4) * g.ny;   // cells x = -2 .. nx + 1
+    unsigned invalid = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % (g.nx + 4)) - 2, y = (int)(i / (g.nx + 4));
+        const int c = node_index(g, x, y);
+        const bool own = x >= 0 && x < g.nx;
+        const bool solid = is_solid(mask, g, x, y);
+        if (own || x == -1 || x == g.nx) {
+            const long long k = (long long)y * w + x + 1;
+            if (!solid && !(isfinite(rho[k]) && rho[k] > 0.0)) invalid = 1;
+            if (!solid && ((ux && !isfinite(ux[k])) || (uy && !isfinite(uy[k])))) invalid = 1;
+        }
+        for (int b = 0; b < 9; ++b) {
+            const bool needed = own || x == -1 || x == g.nx || (x == -2 && kEx[b] == 1) ||
+                                (x == g.nx + 1 && kEx[b] == -1);
+            double v = 0.0;
+            const int xt = x + kEx[b], yt = wrap_index(y + kEy[b], g.ny);
+            if (needed && !solid && xt >= -2 && xt <= g.nx + 1) {
+                const bool back = is_solid(mask, g, xt, yt);
+                // a reflected link is read by the cell itself (only own nodes
+                // and the halo columns x = -1, nx pull); a plain one by the
+                // cell it points to, which must lie in columns -1 .. nx
+                if (back ? (x >= -1 && x <= g.nx) : (xt >= -1 && xt <= g.nx)) {
+                    const long long j = back ? (long long)y * w + x + 1 : (long long)yt * w + xt + 1;
+                    const int bb = back ? kOpp[b] : b;
+                    if (ux == nullptr && uy == nullptr)
+                        v = kWeq[bb] * (rho[j] - rho_ref);
+                    else
+                        v = feq(bb, rho[j], ux ? ux[j] : 0.0, uy ? uy[j] : 0.0) - kWeq[bb] * rho_ref;
+                }
+            }
+            if (own || needed) f[b * g.plane + c] = (T)v;
+        }
+    }
+    if (invalid) bad[lat] = gen;
+}
+
+// Halo of an x-slab, 12 * ny values of the stored type: what the neighbour
+// on `side` (0: left, 1: right) reads from this slab's state, the nine
+// populations of the edge column (its halo ring's node there pulls those
+// that point away from this slab or along the edge, and reads the others
+// back where a link comes from a solid cell), then the three of the next
+// column that point away from this slab. pack reads them from this slab's
+// state; unpack writes a neighbour's packed halo into this slab's frame
+// (side 0: columns -1, -2 from the left neighbour; side 1: columns nx,
+// nx + 1 from the right one).
+constexpr int kHaloRows = 12;
+__constant__ int kHaloOut[2][kHaloRows] = {{0, 1, 2, 3, 4, 5, 6, 7, 8, 3, 6, 7},
+                                           {0, 1, 2, 3, 4, 5, 6, 7, 8, 1, 5, 8}};
+
+template <typename T>
+__global__ void halo_pack_kernel(Geom g, const T* __restrict__ f_base, int side, T* __restrict__ out) {
+    const T* f = f_base + g.f_off;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= g.ny) return;
+    const int x_outer = side == 0 ? 0 : g.nx - 1, x_inner = side == 0 ? 1 : g.nx - 2;
+    for (int k = 0; k < kHaloRows; ++k) {
+        const int x = k < 9 ? x_outer : x_inner;
+        out[(long long)k * g.ny + y] = f[kHaloOut[side][k] * g.plane + node_index(g, x, y)];
+    }
+}
+
+template <typename T>
+__global__ void halo_unpack_kernel(Geom g, T* __restrict__ f_base, int side, const T* __restrict__ in) {
+    T* f = f_base + g.f_off;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= g.ny) return;
+    // the neighbour on the left packed its side 1, the one on the right its side 0
+    const int from = 1 - side;
+    const int x_outer = side == 0 ? -1 : g.nx, x_inner = side == 0 ? -2 : g.nx + 1;
+    for (int k = 0; k < kHaloRows; ++k) {
+        const int x = k < 9 ? x_outer : x_inner;
+        f[kHaloOut[from][k] * g.plane + node_index(g, x, y)] = in[(long long)k * g.ny + y];
+    }
+}
+
 // Pulled distribution of node (x, y) as stored (f_a - w_a rho_ref, or f_a
 // for plain storage), in FP64; false if solid. The density is rho_ref plus
 // their sum (the weights sum to 1) and the momentum their first moment (the
@@ -83,7 +177,7 @@ template <typename T>
 __device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask, int x, int y,
                                             double out[9]) {
     T tmp[9];
-    if (pull_node<T>(f, mask, (int)g.plane, nbr_of(g.nx, g.ny, g.pitch, x, y), tmp)) return false;
+    if (pull_node<T>(f, mask, (int)g.plane, nbr_geom(g, x, y), tmp)) return false;
     for (int a = 0; a < 9; ++a) out[a] = (double)tmp[a];
     return true;
 }
@@ -106,7 +200,7 @@ __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<do
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const Phys<double> P = phys[lat];
-    const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
+    const uint8_t* mask = geom_mask(g) ? mask_base + g.mask_off : nullptr;
     const T* f = f_base + g.f_off;
     double* psi_plane = psi_base + g.f_off / 9;  // one plane per lattice, same indexing
     const long long w = g.nx + 2, n = w * (g.ny + 2);
@@ -151,7 +245,7 @@ __global__ void density_kernel(const Geom* __restrict__ geoms, const Phys<double
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const double rho_ref = phys[lat].rho_ref;
-    const uint8_t* mask = g.has_mask ? mask_base + g.mask_off : nullptr;
+    const uint8_t* mask = geom_mask(g) ? mask_base + g.mask_off : nullptr;
     const T* f = f_base + g.f_off;
     const int n = g.nx * g.ny;  // < 2^31: 9 stored planes hold fewer than 2^31 elements
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -255,6 +349,26 @@ cudaError_t init_impl(const LaunchSet& L, const double* rho, const double* ux, c
 }
 
 template <typename T>
+cudaError_t init_open_impl(const Geom& g, double rho_ref, const double* rho, const double* ux, const double* uy,
+                           const uint8_t* mask, T* f, unsigned* bad, int lat, unsigned gen, cudaStream_t s) {
+    long long cells = (long long)(g.nx + 4) * g.ny;
+    long long blocks = (cells + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    init_open_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(g, rho_ref, rho, ux, uy, mask, f, bad, lat, gen);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t halo_impl(const Geom& g, T* f, int side, T* buf, bool pack, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((g.ny + 127) / 128);
+    if (pack)
+        halo_pack_kernel<T><<<blocks, 128, 0, s>>>(g, f, side, buf);
+    else
+        halo_unpack_kernel<T><<<blocks, 128, 0, s>>>(g, f, side, buf);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t moments_impl(const LaunchSet& L, const T* f, double* psi, double* rho, double* ux, double* uy,
                          double* p, cudaStream_t s) {
     // cells of the nodes plus a one-cell frame: (nx + 2)(ny + 2) <= nodes + 2(nx + ny) + 4
@@ -293,6 +407,22 @@ cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double*
 cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
                             const double* uy, double* f, unsigned* bad, unsigned gen, cudaStream_t s) {
     return init_impl<double>(L, rho, ux, uy, f, bad, gen, s);
+}
+cudaError_t launch_init_open_f32(const Geom& g, double rho_ref, const double* rho, const double* ux,
+                                 const double* uy, const uint8_t* mask, float* f, unsigned* bad, int lat,
+                                 unsigned gen, cudaStream_t s) {
+    return init_open_impl<float>(g, rho_ref, rho, ux, uy, mask, f, bad, lat, gen, s);
+}
+cudaError_t launch_init_open_f64(const Geom& g, double rho_ref, const double* rho, const double* ux,
+                                 const double* uy, const uint8_t* mask, double* f, unsigned* bad, int lat,
+                                 unsigned gen, cudaStream_t s) {
+    return init_open_impl<double>(g, rho_ref, rho, ux, uy, mask, f, bad, lat, gen, s);
+}
+cudaError_t launch_halo_f32(const Geom& g, float* f, int side, float* buf, bool pack, cudaStream_t s) {
+    return halo_impl<float>(g, f, side, buf, pack, s);
+}
+cudaError_t launch_halo_f64(const Geom& g, double* f, int side, double* buf, bool pack, cudaStream_t s) {
+    return halo_impl<double>(g, f, side, buf, pack, s);
 }
 cudaError_t launch_density_f32(const LaunchSet& L, const float* f, double* rho, cudaStream_t s) {
     return density_impl<float>(L, f, rho, s);

@@ -32,9 +32,14 @@ constexpr unsigned FLAG_TIMEOUT = 4u;   // a bounded device-side wait gave up
 constexpr int kGX = 32;  // stored column of node x = 0
 constexpr int kGY = 2;   // stored row of node y = 0
 
-// Geometry of one lattice of the batch.
+// Geometry of one lattice of the batch. flags: kGeomMask (a wall mask) and
+// kGeomOpenX (an x-slab of a lattice split across contexts: its x edges are
+// not periodic; the pulls across them read the frame columns x = -2, -1 and
+// nx, nx + 1, which the halo exchange fills).
+constexpr int kGeomMask = 1;
+constexpr int kGeomOpenX = 2;
 struct Geom {
-    int nx, ny, pitch, has_mask;
+    int nx, ny, pitch, flags;
     long long f_off;     // element offset of plane 0 in the distribution arrays
     long long plane;     // elements per plane ((ny + 2 kGY) * pitch)
     long long mask_off;  // byte offset of this lattice's mask plane
@@ -44,6 +49,8 @@ struct Geom {
 __host__ __device__ __forceinline__ int node_index(const Geom& g, int x, int y) {
     return (y + kGY) * g.pitch + x + kGX;
 }
+__host__ __device__ __forceinline__ bool geom_mask(const Geom& g) { return (g.flags & kGeomMask) != 0; }
+__host__ __device__ __forceinline__ bool geom_open_x(const Geom& g) { return (g.flags & kGeomOpenX) != 0; }
 
 // Physical parameters of one lattice in the arithmetic type T.
 template <typename T>
@@ -91,20 +98,25 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 // neighbour across an edge is the node at the far side of the same row or
 // column. x in [-1, nx] and y in [-1, ny] (one period outside at most) are
 // first brought into the lattice, so a halo cell beside an edge is the node
-// it stands for. Valid for any nx, ny >= 1.
+// it stands for. Valid for any nx, ny >= 1. With open_x (an x-slab) x is not
+// wrapped: x = -1 and x = nx are the frame columns that hold the neighbouring
+// slabs' edge columns, and their x neighbours the next frame columns.
 struct Nbr {
     int c, xm, xp, ym, yp;
 };
-__device__ __forceinline__ Nbr nbr_of(int nx, int ny, int pitch, int x, int y) {
-    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+__device__ __forceinline__ Nbr nbr_of(int nx, int ny, int pitch, int x, int y, bool open_x = false) {
+    if (!open_x) x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
     y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
     Nbr n;
     n.c = (y + kGY) * pitch + x + kGX;
-    n.xm = x == 0 ? nx - 1 : -1;
-    n.xp = x == nx - 1 ? 1 - nx : 1;
+    n.xm = (x == 0 && !open_x) ? nx - 1 : -1;
+    n.xp = (x == nx - 1 && !open_x) ? 1 - nx : 1;
     n.ym = y == 0 ? (ny - 1) * pitch : -pitch;
     n.yp = y == ny - 1 ? (1 - ny) * pitch : pitch;
     return n;
+}
+__device__ __forceinline__ Nbr nbr_geom(const Geom& g, int x, int y) {
+    return nbr_of(g.nx, g.ny, g.pitch, x, y, geom_open_x(g));
 }
 
 // psi of Eq. 13 with the CS pressure of Eq. 15, written as

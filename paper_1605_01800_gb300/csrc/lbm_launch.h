@@ -107,6 +107,21 @@ cudaError_t launch_init_f32(const LaunchSet& L, const double* rho, const double*
 cudaError_t launch_init_f64(const LaunchSet& L, const double* rho, const double* ux,
                             const double* uy, double* f, unsigned* bad, unsigned gen, cudaStream_t s);
 
+// Initial state of one lattice open in x (an x-slab): rho/ux/uy are device
+// arrays of (nx + 2) x ny values, the neighbouring slabs' edge columns
+// included (ux/uy may be null); `mask` is the device mask base.
+cudaError_t launch_init_open_f32(const Geom& g, double rho_ref, const double* rho, const double* ux,
+                                 const double* uy, const uint8_t* mask, float* f, unsigned* bad, int lat,
+                                 unsigned gen, cudaStream_t s);
+cudaError_t launch_init_open_f64(const Geom& g, double rho_ref, const double* rho, const double* ux,
+                                 const double* uy, const uint8_t* mask, double* f, unsigned* bad, int lat,
+                                 unsigned gen, cudaStream_t s);
+// Halo of an x-slab (12 * ny values): pack what the neighbour on `side` reads
+// from the state `f` into `buf`, or unpack a neighbour's halo from `buf`
+// into the frame of `f` (pack = false).
+cudaError_t launch_halo_f32(const Geom& g, float* f, int side, float* buf, bool pack, cudaStream_t s);
+cudaError_t launch_halo_f64(const Geom& g, double* f, int side, double* buf, bool pack, cudaStream_t s);
+
 // rho, v (Eq. 6), p (Eq. 10) into device arrays indexed like the init inputs
 // (all four required), computed in FP64 from the stored distribution; psi is
 // scratch of one plane per lattice in the stored layout (element offset

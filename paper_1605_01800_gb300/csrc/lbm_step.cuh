@@ -370,7 +370,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
     constexpr int NT = TX * TYT;
     constexpr int NH = 2 * SW + 2 * TY;  // halo ring cells
     const T* __restrict__ fin = A.fin + g.f_off;
-    const uint8_t* __restrict__ mask = g.has_mask ? A.mask + g.mask_off : nullptr;
+    const uint8_t* __restrict__ mask = geom_mask(g) ? A.mask + g.mask_off : nullptr;
     const int plane = (int)g.plane;
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
     const T rho_ref = P.rho_ref;
@@ -389,7 +389,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
     for (int r = 0; r < RY; ++r) {
         const int y = y0 + r;
         live[r] = (x <= nx) && (y <= ny);
-        if (live[r]) live[r] = !pull_node<T>(fin, mask, plane, nbr_of(nx, ny, pitch, x, y), f[r]);
+        if (live[r]) live[r] = !pull_node<T>(fin, mask, plane, nbr_geom(g, x, y), f[r]);
     }
 
     // ---- halo ring: psi only (issued before the own nodes' arithmetic)
@@ -417,7 +417,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
             hc[k] = cy * SW + cx;
             const int hx = tile.x0 - 1 + cx, hy = tile.y0 - 1 + cy;
             T fh[9];
-            if (hx <= nx && hy <= ny && !pull_node<T>(fin, mask, plane, nbr_of(nx, ny, pitch, hx, hy), fh)) {
+            if (hx <= nx && hy <= ny && !pull_node<T>(fin, mask, plane, nbr_geom(g, hx, hy), fh)) {
                 if constexpr (std::is_same<T, float>::value)
                     ph[k] = f32_halo_psi(fh, rho_ref, P, flag);
                 else

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
     // thread 0: arm stage s for tile t and issue its box loads
     auto issue = [&](int t, int s) {
         const Tile tl = A.tiles[t];
-        const int has_mask = A.geom[tl.lat].has_mask;
+        const bool has_mask = geom_mask(A.geom[tl.lat]);
         unsigned char* st = smem + s * B::STAGE_BYTES;
         mbar_arrive_expect_tx(&bars[s], 9 * B::BOX_BYTES + (has_mask ? B::MASK_BYTES : 0) + A.extra_tx);
         const CUtensorMap* fm = &M.f[tl.lat];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
         const Phys<float>& P = *Pp;
         const float* __restrict__ st = reinterpret_cast<const float*>(smem + s * B::STAGE_BYTES);
         const uint8_t* __restrict__ ms =
-            g.has_mask ? reinterpret_cast<const uint8_t*>(smem + s * B::STAGE_BYTES + 9 * B::BOX_BYTES) : nullptr;
+            geom_mask(g) ? reinterpret_cast<const uint8_t*>(smem + s * B::STAGE_BYTES + 9 * B::BOX_BYTES) : nullptr;
         const float rho_ref = P.rho_ref;
         unsigned flag = 0;
 
@@ -377,7 +377,7 @@ bool encode_lattice_maps(const Geom& g, int tx, int ty, const float* buf0, const
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return false;
     }
-    if (g.has_mask) {
+    if (geom_mask(g)) {
         const cuuint64_t mdims[2] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * kGY)};
         const cuuint64_t mstr[1] = {(cuuint64_t)g.pitch};
         const cuuint32_t mbox[2] = {(cuuint32_t)(tx + 32), (cuuint32_t)(ty + 4)};

@@ -40,6 +40,7 @@ EXPORTED = [
     "lbm_clear_status", "lbm_sync", "lbm_state_size", "lbm_save_state", "lbm_load_state",
     "lbm_tile_count", "lbm_tile_shape", "lbm_tile_kind", "lbm_set_tile", "lbm_autotune", "lbm_info",
     "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc", "lbm_get_state_view",
+    "lbm_set_open_x", "lbm_halo_pack", "lbm_halo_unpack",
 ]
 
 
@@ -132,6 +133,9 @@ def load(build_if_missing: bool = True):
     lib.lbm_last_error.argtypes = []
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_total_mass_fp32_noalloc.argtypes = [_vp, I, I, ctypes.c_double, _vp, _vp, _vp]
+    lib.lbm_set_open_x.argtypes = [_ctx, I, _vp]
+    lib.lbm_halo_pack.argtypes = [_ctx, I, I, _vp]
+    lib.lbm_halo_unpack.argtypes = [_ctx, I, I, _vp]
     lib.lbm_destroy.argtypes = [_ctx]
     lib.lbm_destroy.restype = None
     for name in EXPORTED:
@@ -184,6 +188,25 @@ def lbm_init_fields(ctx, lat, rho, ux=None, uy=None):
 
 def lbm_init_fields_all(ctx, rho, ux=None, uy=None):
     _check(load().lbm_init_fields_all(ctx, _ptr(rho), _ptr(ux), _ptr(uy)))
+
+
+LBM_HALO_ROWS = 12   # values per lattice row in a packed halo (lbm.h)
+
+
+def lbm_set_open_x(ctx, lat, halo_mask=None):
+    """Mark lattice `lat` as an x-slab (lbm.h): halo_mask None or (4, ny) bytes."""
+    hm = None
+    if halo_mask is not None:
+        hm = np.ascontiguousarray(halo_mask, dtype=np.uint8)
+    _check(load().lbm_set_open_x(ctx, lat, None if hm is None else hm.ctypes.data))
+
+
+def lbm_halo_pack(ctx, lat, side, dev_out_ptr):
+    _check(load().lbm_halo_pack(ctx, lat, int(side), ctypes.c_void_p(dev_out_ptr)))
+
+
+def lbm_halo_unpack(ctx, lat, side, dev_in_ptr):
+    _check(load().lbm_halo_unpack(ctx, lat, int(side), ctypes.c_void_p(dev_in_ptr)))
 
 
 def lbm_step(ctx, n):

@@ -1,0 +1,133 @@
+"""One lattice split into x-slabs on the GPU (lbm_set_open_x, lbm_halo_pack,
+lbm_halo_unpack): the slabs, stepped with a halo exchange after every step,
+equal the undivided lattice bit for bit, in FP32 deviation storage and FP64,
+with walls along the cut and slab widths that do not fill whole tiles.
+
+The exchange runs between contexts of one process (device copies) and
+between two gloo ranks sharing the one GPU (host copies and point-to-point
+messages; the ranks' kernels never wait on each other: every wait is on the
+host)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1605_01800_gb300 import lbm, xslab
+from tests.cases import small_spec
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 25
+
+
+def _spec():
+    # a vapour bubble between two walls (rows 0 and ny - 1), with noise
+    return small_spec(96, 40, tr=0.6, walls=True, seed=271, shape="bubble", R=12.0)
+
+
+def _whole(spec, precision, steps):
+    b = lbm.Batch([spec], precision)
+    b.init()
+    b.step(steps)
+    out = b.moments(0)
+    mass = b.mass(0)
+    b.close()
+    return out, mass
+
+
+def _first_of(kind):
+    return next(t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) == kind)
+
+
+@pytest.mark.parametrize("precision,kind", [("fp32_dev", lbm.LBM_TILE_PLAIN), ("fp32_dev", lbm.LBM_TILE_TMA),
+                                            ("fp32_dev", lbm.LBM_TILE_PIPELINED), ("fp64", lbm.LBM_TILE_PLAIN)])
+def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind):
+    """Every step-kernel kind on the slabs (the TMA and pipelined kernels take
+    the slabs' interior tiles, the plain kernel's general path the tiles
+    along the cuts)."""
+    spec = _spec()
+    ref, mass = _whole(spec, precision, STEPS)
+    slabs = xslab.LocalSlabs(spec, [0, 37, 59, 96], precision)   # widths 37, 22, 37
+    tile = 1 if kind == lbm.LBM_TILE_PLAIN else _first_of(kind)
+    for s in slabs.slabs:
+        lbm.lbm_set_tile(s.batch.ctx, tile)
+    slabs.step(STEPS)
+    got = slabs.moments()
+    for name, a, b in zip(("rho", "ux", "uy", "p"), got, ref):
+        assert np.array_equal(a, b), name
+    # the mass of the stored state adds up across the slabs
+    assert sum(s.batch.mass(0) for s in slabs.slabs) == pytest.approx(mass, rel=1e-12)
+    slabs.close()
+
+
+def test_open_lattice_rules():
+    spec = _spec()
+    slab, rho_ext, halo = xslab.cut(spec, 0, 48)
+    b = lbm.Batch([slab], "fp32_dev")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_halo_pack(b.ctx, 0, 0, 1)           # not open yet
+    assert e.value.code == lbm.LBM_EINVAL
+    lbm.lbm_set_open_x(b.ctx, 0, halo)
+    b.init([rho_ext])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_step(b.ctx, 2)                      # a halo exchange is due after every step
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_init_fields_all(b.ctx, np.ascontiguousarray(slab.rho.ravel()))
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_halo_pack(b.ctx, 0, 2, 1)           # side 0 or 1
+    lbm.lbm_step(b.ctx, 1)
+    b.close()
+    auto = small_spec(16, 8, seed=3)
+    auto.rho_ref = -1.0                             # automatic reference: refused for a slab
+    b = lbm.Batch([auto], "fp32_dev")
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_set_open_x(b.ctx, 0, None)
+    b.close()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q, steps):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    spec = _spec()
+    cuts = [0, 41, 96]
+    mine = xslab.RankSlab(spec, "fp32_dev", cuts=cuts)
+    mine.step(steps)
+    # each rank's columns in a whole-lattice array, zero elsewhere (equal
+    # shapes for the gather; the sum over ranks is exact)
+    full = torch.zeros((spec.ny, spec.nx), dtype=torch.float64)
+    full[:, cuts[rank]:cuts[rank + 1]] = torch.from_numpy(mine.moments()[0].copy())
+    got = [torch.zeros_like(full) for _ in range(world)]
+    dist.all_gather(got, full)
+    if rank == 0:
+        q.put(sum(g.numpy() for g in got))
+    mine.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_on_one_gpu_equal_the_whole_lattice():
+    import torch.multiprocessing as mp
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, STEPS)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    (ref, _, _, _), _ = _whole(_spec(), "fp32_dev", STEPS)
+    assert np.array_equal(got, ref)
