@@ -18,9 +18,10 @@ lattice (1.2 GB) on which the sustained HBM fraction is measured. `e2e` times
 the public C ABI with host buffers: upload of every density field, one step,
 download of every density field. `cpu_baseline` times the FP64 CPU oracle on a
 bounded sample, on every host core. Under torchrun every rank advances its own
-copy of the batch (weak scaling, no collective on the data path), and the
+copy of the batch (weak scaling, no collective on the data path); the
 48-lattice Laplace batch is also split across the ranks by node count
-(`sharded`, strong scaling).
+(`sharded`, strong scaling), and the collapse lattice into one x-slab per rank
+with a halo exchange after every step (`xslab`, strong scaling).
 """
 import argparse
 import hashlib
@@ -435,6 +436,30 @@ def main():
                    "ms_per_step": sms, "MLUPS": lnodes / (sms * 1e-3) / 1e6,
                    "note": "LPT shares by node count, each rank steps its own share, max over ranks"}
 
+    # ---- one lattice split into x-slabs across the ranks (strong scaling):
+    # the collapse lattice, each rank its slab, a halo exchange after every
+    # step (NCCL point-to-point); reported, not fatal, if it fails
+    xsl = None
+    if world > 1:
+        try:
+            from paper_1605_01800_gb300 import xslab
+            (cspec,) = inputs.collapse()
+            rs = xslab.RankSlab(cspec, "fp32_dev", stream=stream)
+            rs.step(10)
+            barrier()
+            t0 = time.perf_counter()
+            k_x = 200
+            rs.step(k_x)
+            barrier()
+            xs = max_over_ranks(time.perf_counter() - t0)
+            rs.close()
+            xsl = {"workload": "collapse_2048x1024", "ranks": world, "steps": k_x, "ms_per_step": 1e3 * xs / k_x,
+                   "MLUPS": cspec.nodes * k_x / xs / 1e6,
+                   "note": "x-slabs, one per rank, halo exchange (12 values per row and face) after every step, "
+                           "wall-clock over the ranks"}
+        except Exception as exc:  # the headline line must still be printed
+            xsl = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+
     # ---- e2e through the C ABI with host buffers
     rho_in = torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
     rho_in[:] = np.concatenate([s.rho.ravel() for s in specs])
@@ -533,6 +558,8 @@ def main():
     }
     if sharded is not None:
         line["sharded"] = sharded
+    if xsl is not None:
+        line["xslab"] = xsl
     if rank == 0 and world == 1:
         cores = host_cores()
         cpu_mlups, cpu_steps, cpu_s, used = time_oracle(specs, args.cpu_seconds, threads=cores)

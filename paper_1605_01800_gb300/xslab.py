@@ -129,16 +129,20 @@ class RankSlab:
         import torch.distributed as dist
         s = self.slab
         left, right = (self.rank - 1) % self.world, (self.rank + 1) % self.world
+        # everything on the slab's stream: under NCCL the sends read the
+        # packed buffers after the pack, and wait() orders the unpack after
+        # the receives; under gloo the copies to the host synchronise it
         with torch.cuda.stream(self.stream):
             s.pack()
-        self.stream.synchronize()
-        out = [t.cpu() for t in s.out] if self.host else s.out
-        inc = [torch.empty_like(t) for t in out] if self.host else s.inc
-        ops = [dist.P2POp(dist.isend, out[1], right, tag=1), dist.P2POp(dist.irecv, inc[0], left, tag=1),
-               dist.P2POp(dist.isend, out[0], left, tag=0), dist.P2POp(dist.irecv, inc[1], right, tag=0)]
-        for r in dist.batch_isend_irecv(ops):
-            r.wait()
-        with torch.cuda.stream(self.stream):
+            if self.host:
+                out = [t.cpu() for t in s.out]
+                inc = [torch.empty_like(t) for t in out]
+            else:
+                out, inc = s.out, s.inc
+            ops = [dist.P2POp(dist.isend, out[1], right, tag=1), dist.P2POp(dist.irecv, inc[0], left, tag=1),
+                   dist.P2POp(dist.isend, out[0], left, tag=0), dist.P2POp(dist.irecv, inc[1], right, tag=0)]
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
             if self.host:
                 s.inc[0].copy_(inc[0])
                 s.inc[1].copy_(inc[1])
