@@ -45,7 +45,7 @@ SUSTAINED_PROFILES = {"roofline_4096": os.path.join(ROOT, "profiles", "step_fp32
 SUSTAINED = ("laplace_batch", "collapse_2048x1024", "roofline_4096", "collapse_x8")
 # device sources of each step-kernel kind whose ncu traffic the profile records
 # (a pipelined step also launches the plain kernel on its other tiles)
-_PLAIN = ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu")
+_PLAIN = ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu", "lbm_step_f32.inc")
 KERNEL_SOURCES = {kind: [os.path.join(ROOT, "paper_1605_01800_gb300", "csrc", f) for f in files]
                   for kind, files in (("plain", _PLAIN), ("pipelined", _PLAIN + ("lbm_step_pipe.cu",)))}
 

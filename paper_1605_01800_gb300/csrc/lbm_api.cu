@@ -546,7 +546,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
     if (c->precision == LBM_FP64) {
         StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
                            (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-        e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream);
+        e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream, any_open_x(c));
     } else if (is_pipe(c->tile_index)) {
         const int v = c->tile_index - pipe_first();
         const PhysTable<float>* table = c->n <= kParamLattices ? c->h_table : nullptr;
@@ -555,7 +555,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         if (e == cudaSuccess && c->n_tiles > 0) {
             StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
                               (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-            e = launch_step_f32(pipe_plain_partner(v), c->n_tiles, a, c->h_table, c->stream);
+            e = launch_step_f32(pipe_plain_partner(v), c->n_tiles, a, c->h_table, c->stream, any_open_x(c));
         }
     } else if (c->tile_index >= kTileCount) {
         const int v = c->tile_index - kTileCount;
@@ -565,12 +565,12 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
         if (e == cudaSuccess && c->n_tiles > 0) {
             StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
                               (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-            e = launch_step_f32(tma_plain_partner(v), c->n_tiles, a, c->h_table, c->stream);
+            e = launch_step_f32(tma_plain_partner(v), c->n_tiles, a, c->h_table, c->stream, any_open_x(c));
         }
     } else {
         StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
                           (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-        e = launch_step_f32(c->tile_index, c->n_tiles, a, c->h_table, c->stream);
+        e = launch_step_f32(c->tile_index, c->n_tiles, a, c->h_table, c->stream, any_open_x(c));
     }
     return e;
 }

@@ -84,9 +84,19 @@ cudaError_t launch_step_pipe(int v, int grid, const PipeArgs& a, const PhysTable
 
 // table: the batch's parameters for the constant-bank path (batches of at
 // most kParamLattices lattices), or null to read them from global memory.
-cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a,
-                            const PhysTable<float>* table, cudaStream_t s);
-cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s);
+// open: the batch holds lattices open in x (x-slabs); their kernels are
+// instantiated apart from the ordinary ones.
+cudaError_t launch_step_f32_closed(int tile_index, int n_tiles, const StepArgs<float>& a,
+                                   const PhysTable<float>* table, cudaStream_t s);
+cudaError_t launch_step_f32_open(int tile_index, int n_tiles, const StepArgs<float>& a,
+                                 const PhysTable<float>* table, cudaStream_t s);
+inline cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a,
+                                   const PhysTable<float>* table, cudaStream_t s, bool open = false) {
+    return open ? launch_step_f32_open(tile_index, n_tiles, a, table, s)
+                : launch_step_f32_closed(tile_index, n_tiles, a, table, s);
+}
+cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s,
+                            bool open = false);
 
 // Lattices [lat0, lat0 + n_lat) of a context, for the FP64 helper kernels.
 struct LaunchSet {

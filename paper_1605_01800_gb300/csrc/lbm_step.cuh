@@ -361,7 +361,10 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
 }
 
 // One tile by the general path (any tile: partial, walled, tiny lattices).
-template <typename T, int TX, int TYT, int RY>
+// OPEN: the batch may hold lattices open in x (x-slabs), whose pulls across
+// the x edges read the frame instead of wrapping; instantiated apart, so
+// that the kernels of ordinary batches compile as if slabs did not exist.
+template <typename T, int TX, int TYT, int RY, bool OPEN>
 __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& tile, const Geom& g,
                                              const Phys<T>& P, T* s_psi) {
     constexpr int TY = TYT * RY;
@@ -389,7 +392,8 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
     for (int r = 0; r < RY; ++r) {
         const int y = y0 + r;
         live[r] = (x <= nx) && (y <= ny);
-        if (live[r]) live[r] = !pull_node<T>(fin, mask, plane, nbr_geom(g, x, y), f[r]);
+        if (live[r])
+            live[r] = !pull_node<T>(fin, mask, plane, OPEN ? nbr_geom(g, x, y) : nbr_of(nx, ny, pitch, x, y), f[r]);
     }
 
     // ---- halo ring: psi only (issued before the own nodes' arithmetic)
@@ -417,7 +421,8 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
             hc[k] = cy * SW + cx;
             const int hx = tile.x0 - 1 + cx, hy = tile.y0 - 1 + cy;
             T fh[9];
-            if (hx <= nx && hy <= ny && !pull_node<T>(fin, mask, plane, nbr_geom(g, hx, hy), fh)) {
+            if (hx <= nx && hy <= ny &&
+                !pull_node<T>(fin, mask, plane, OPEN ? nbr_geom(g, hx, hy) : nbr_of(nx, ny, pitch, hx, hy), fh)) {
                 if constexpr (std::is_same<T, float>::value)
                     ph[k] = f32_halo_psi(fh, rho_ref, P, flag);
                 else
@@ -481,8 +486,10 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
 
 // MINB: minimum resident CTAs per SM the register allocation must allow
 // (the register cap is 65536 / (MINB * TX * TYT) per thread). One CTA per
-// tile; full tiles of wall-free lattices take the FP32 fast path.
-template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE>
+// tile; full tiles of wall-free lattices take the FP32 fast path (an
+// x-slab's tiles along its cuts are never marked clear). OPEN: see
+// tile_general.
+template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE, bool OPEN = false>
 __global__ void __launch_bounds__(TX * TYT, MINB)
     step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT) {
     constexpr int TY = TYT * RY;
@@ -520,7 +527,7 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
             return;
         }
     }
-    tile_general<T, TX, TYT, RY>(A, tile, g, P, s_psi);
+    tile_general<T, TX, TYT, RY, OPEN>(A, tile, g, P, s_psi);
 }
 
 }  // namespace lbm
