@@ -61,6 +61,19 @@ def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind):
     slabs.close()
 
 
+def test_narrow_slabs_equal_the_whole_lattice():
+    """Five slabs, two of them at the minimum width of 2 columns and one of
+    3: every node of those slabs is an edge node whose pulls and psi ring
+    reach into both neighbours' halos."""
+    spec = _spec()
+    ref, _ = _whole(spec, "fp32_dev", STEPS)
+    slabs = xslab.LocalSlabs(spec, [0, 2, 5, 40, 42, 96], "fp32_dev")
+    slabs.step(STEPS)
+    for name, a, b in zip(("rho", "ux", "uy", "p"), slabs.moments(), ref):
+        assert np.array_equal(a, b), name
+    slabs.close()
+
+
 def test_open_lattice_rules():
     spec = _spec()
     slab, rho_ext, halo = xslab.cut(spec, 0, 48)
