@@ -58,6 +58,8 @@ def _load():
         lib.oracle_moments.restype = ctypes.c_uint
         lib.oracle_mass.argtypes = [P, _dp]
         lib.oracle_mass.restype = ctypes.c_double
+        lib.oracle_momentum.argtypes = [P, _dp, _dp, _dp, _dp]
+        lib.oracle_momentum.restype = ctypes.c_uint
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_openmp.restype = ctypes.c_int
         _lib = lib
@@ -131,6 +133,14 @@ class Lattice:
 
     def mass(self):
         return self.lib.oracle_mass(ctypes.byref(self.p), _ptr(self.f))
+
+    def momentum(self):
+        """(sum of rho vx, sum of rho vy) over the fluid nodes, Eq. 6."""
+        work = np.zeros(2 * self.nx * self.ny)
+        px, py = ctypes.c_double(), ctypes.c_double()
+        self.lib.oracle_momentum(ctypes.byref(self.p), _ptr(self.f), _ptr(work),
+                                 ctypes.byref(px), ctypes.byref(py))
+        return px.value, py.value
 
     def force_from_psi(self, psi):
         psi = np.ascontiguousarray(psi, dtype=np.float64).reshape(self.ny, self.nx)

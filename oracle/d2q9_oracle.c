@@ -485,3 +485,31 @@ double oracle_mass(const oracle_params* P, const double* f) {
     }
     return m;
 }
+
+/* Total momentum over the fluid nodes: the sums of rho v of Eq. 6,
+ * j + F/2 with j = sum_a e_a f_a and F of Eq. 7, summed in node order.
+ * work must hold 2*N doubles. Returns the psi flags of the density sweep. */
+unsigned oracle_momentum(const oracle_params* P, const double* f, double* work,
+                         double* px, double* py) {
+    size_t N = (size_t)P->nx * P->ny;
+    double* rho = work;
+    double* psi = work + N;
+    unsigned flag = sweep_density_psi(P, f, rho, psi);
+    double sx = 0.0, sy = 0.0;
+    for (int y = 0; y < P->ny; ++y)
+        for (int x = 0; x < P->nx; ++x) {
+            if (is_solid(P, x, y)) continue;
+            size_t i = (size_t)y * P->nx + x;
+            double Fx, Fy, jx = 0.0, jy = 0.0;
+            force_at(P, psi, x, y, &Fx, &Fy, NULL);
+            for (int a = 0; a < Q; ++a) {
+                jx += EX[a] * f[(size_t)a * N + i];
+                jy += EY[a] * f[(size_t)a * N + i];
+            }
+            sx += jx + 0.5 * Fx;
+            sy += jy + 0.5 * Fy;
+        }
+    *px = sx;
+    *py = sy;
+    return flag;
+}

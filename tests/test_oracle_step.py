@@ -225,6 +225,72 @@ def test_momentum_conserved_periodic():
     assert abs(p1[0] - p0[0]) < 1e-13 * scale and abs(p1[1] - p0[1]) < 1e-13 * scale
 
 
+def _stratified_at_rest(nx, ny, along_x):
+    """Walls on two opposite edges, a density that varies only across them
+    (a diffuse interface with a trend), at rest."""
+    Tc, _, _ = thermo.critical_point()
+    rg, rl, _ = thermo.maxwell(0.6 * Tc)
+    n = nx if along_x else ny
+    k = np.arange(n, dtype=float)
+    prof = 0.5 * (rl + rg) + 0.5 * (rl - rg) * np.tanh((k - 0.4 * n) / 3.0) + 0.002 * k
+    rho = np.tile(prof, (ny, 1)) if along_x else np.tile(prof[:, None], (1, nx))
+    solid = np.zeros((ny, nx), np.uint8)
+    if along_x:
+        solid[:, 0] = solid[:, nx - 1] = 1
+    else:
+        solid[0, :] = solid[ny - 1, :] = 1
+    L = d2q9.Lattice(nx, ny, T=0.6 * Tc, s=[1, 1.1, 1.1, 1, 1.1, 1, 1.1, 1.25, 1.25], eps=1.86, solid=solid)
+    L.init(rho)
+    return L, prof
+
+
+@pytest.mark.parametrize("along_x", [False, True])
+def test_total_momentum_at_rest_is_half_the_wall_reaction(along_x):
+    # At rest j = 0, so the total is sum F / 2. For a field that varies only
+    # across the channel, Eq. 7 gives F_n(k) = -G psi_k (psi_{k+1} - psi_{k-1})
+    # / 2 (axis weight 1/3 plus two diagonals of 1/12), a wall neighbour
+    # taking psi_k. The sum over the fluid layers telescopes to
+    # -G (psi_last^2 - psi_first^2) / 2 per line, so the total momentum along
+    # the normal is -G * lines * (psi_last^2 - psi_first^2) / 4 and zero along
+    # the walls.
+    nx, ny = (24, 7) if along_x else (7, 24)
+    L, prof = _stratified_at_rest(nx, ny, along_x)
+    lines = ny if along_x else nx
+    n = len(prof)
+    psi_first, f1 = L.psi(prof[1])
+    psi_last, f2 = L.psi(prof[n - 2])
+    assert f1 == 0 and f2 == 0
+    G = -1.0
+    normal = -G * lines * (psi_last ** 2 - psi_first ** 2) / 4
+    px, py = L.momentum()
+    along, across = (px, py) if along_x else (py, px)
+    assert abs(normal) > 1e-3
+    assert along == pytest.approx(normal, rel=1e-12)
+    assert abs(across) < 1e-15 * abs(normal)
+
+
+def test_total_momentum_of_a_uniform_drift():
+    # uniform density: F = 0, and f_eq(rho, u) carries j = rho u (Eq. 4)
+    nx, ny, rho0, ux, uy = 11, 6, 0.31, 0.013, -0.021
+    L = d2q9.Lattice(nx, ny, T=0.6 * 0.0943287, s=[1, 1.1, 1.1, 1, 1.1, 1, 1.1, 1.5, 1.5], eps=1.86)
+    L.init(np.full((ny, nx), rho0), np.full((ny, nx), ux), np.full((ny, nx), uy))
+    px, py = L.momentum()
+    assert px == pytest.approx(nx * ny * rho0 * ux, rel=1e-13)
+    assert py == pytest.approx(nx * ny * rho0 * uy, rel=1e-13)
+
+
+def test_total_momentum_is_invariant_without_walls():
+    L = _droplet_lattice(40, 36, 0.7, 1.86, 0.6)
+    rho, _, _, _ = L.moments()
+    L.init(rho, np.full_like(rho, 0.01), np.full_like(rho, -0.005))
+    p0 = L.momentum()
+    L.step(200)
+    p1 = L.momentum()
+    scale = L.mass()
+    assert abs(p0[0] - 0.01 * scale) < 1e-3 * abs(p0[0])   # the drift, up to F/2 of the droplet
+    assert abs(p1[0] - p0[0]) < 1e-13 * scale and abs(p1[1] - p0[1]) < 1e-13 * scale
+
+
 def test_pressure_eq10_equals_eos_eq15():
     # With psi from Eq. 13, the LB pressure of Eq. 10 is the CS EOS (Sec. 2.2).
     Tc, _, _ = thermo.critical_point()
