@@ -29,7 +29,8 @@
  *     that return data to the host synchronise that stream.
  *   - Device-side errors (psi^2 < 0 clamped, a non-finite density) are sticky
  *     per lattice; they are reported by lbm_status() and turn the return code
- *     of lbm_read_moments*, lbm_total_mass and lbm_sync into
+ *     of lbm_read_moments*, lbm_total_mass, lbm_total_momentum,
+ *     lbm_totals_all and lbm_sync into
  *     LBM_EPSI_DOMAIN or LBM_ENONFINITE (the data is still written).
  *   - A context is not thread-safe; distinct contexts may be used from
  *     distinct threads.
@@ -204,6 +205,24 @@ int lbm_read_moments_all(lbm_ctx* ctx, double* rho, double* ux, double* uy, doub
 /* Total mass sum_x rho(x) over the fluid nodes of lattice `lat`, reduced in
  * FP64 in a fixed order (bitwise reproducible). Synchronises the stream. */
 int lbm_total_mass(lbm_ctx* ctx, int lat, double* mass);
+
+/* Total momentum of lattice `lat`: the sums over its fluid nodes of
+ * j + F/2, the numerator of Eq. 6 (j = sum_a e_a f_a with the distribution as
+ * lbm_read_moments gathers it, F the force of Eq. 7), i.e. the sums of rho v_x
+ * and rho v_y. Reduced in FP64 in a fixed order (bitwise reproducible). px or
+ * py may be NULL (not both: LBM_EINVAL). Without walls the total is invariant
+ * under lbm_step up to rounding; walls exchange momentum with the fluid.
+ * Three kernel launches; uses the read-out scratch; synchronises the stream.
+ * Returns a lattice's sticky status like lbm_total_mass. */
+int lbm_total_momentum(lbm_ctx* ctx, int lat, double* px, double* py);
+
+/* Mass and momentum of every lattice in three launches for the whole batch:
+ * out (host, 3 * n_lattices doubles) receives, for lattice k in creation
+ * order, out[3k] = lbm_total_mass (bit for bit), out[3k + 1], out[3k + 2] =
+ * lbm_total_momentum. 24 bytes per lattice come back to the host, so a
+ * caller can monitor a large batch every K steps. Returns LBM_EINVAL for a
+ * NULL out, else like lbm_read_moments_all. */
+int lbm_totals_all(lbm_ctx* ctx, double* out);
 
 /* Sticky status bits LBM_FLAG_* of lattice `lat` (0 if clean). Synchronises. */
 int lbm_status(lbm_ctx* ctx, int lat, uint32_t* flags);

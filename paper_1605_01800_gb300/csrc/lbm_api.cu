@@ -870,8 +870,9 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (!rc) rc = dev_alloc(c, &c->d_phys_f, n * sizeof(Phys<float>));
     if (!rc) rc = dev_alloc(c, &c->d_phys_d, n * sizeof(Phys<double>));
     if (!rc) rc = dev_alloc(c, &c->d_status, n * sizeof(unsigned));
-    if (!rc) rc = dev_alloc(c, &c->d_partials, kMassBlocks * sizeof(double));
-    if (!rc) rc = dev_alloc(c, &c->d_scalar, sizeof(double));
+    // reduction scratch: 4 partial sums per block and lattice, 3 totals per lattice
+    if (!rc) rc = dev_alloc(c, &c->d_partials, 4 * (size_t)kMassBlocks * n * sizeof(double));
+    if (!rc) rc = dev_alloc(c, &c->d_scalar, 3 * (size_t)n * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->total_nodes * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_psi, ((size_t)c->total_elems / 9 + 64) * sizeof(double));
     if (!rc && cudaHostAlloc((void**)&c->h_bad, n * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess) {
@@ -1050,6 +1051,54 @@ int lbm_total_mass(lbm_ctx* c, int lat, double* mass) {
     rc = read_status(c, st);
     if (rc) return rc;
     return status_code(st[lat]);
+}
+
+namespace {
+
+// Mass and momentum of lattices [lat0, lat0 + n_lat) into out[3k .. 3k + 2];
+// the status bits of every lattice come back in st.
+int totals_range(lbm_ctx* c, int lat0, int n_lat, double* out, std::vector<unsigned>& st) {
+    const long long N = c->total_nodes;
+    const LaunchSet ls = launch_set(c, lat0, n_lat);
+    cudaError_t e;
+    if (c->precision == LBM_FP64)
+        e = launch_totals_f64(ls, (const double*)c->f[c->cur], c->d_psi, c->d_io, c->d_io + N, c->d_io + 2 * N,
+                              c->d_partials, c->d_scalar, c->stream);
+    else
+        e = launch_totals_f32(ls, (const float*)c->f[c->cur], c->d_psi, c->d_io, c->d_io + N, c->d_io + 2 * N,
+                              c->d_partials, c->d_scalar, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "totals kernels");
+    c->launches += 3;
+    CK(cudaMemcpyAsync(out, c->d_scalar, 3 * (size_t)n_lat * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c, st);
+}
+
+}  // namespace
+
+int lbm_total_momentum(lbm_ctx* c, int lat, double* px, double* py) {
+    Range range("lbm_total_momentum");
+    int rc = check_lat(c, lat);
+    if (rc) return rc;
+    if (!px && !py) return fail(LBM_EINVAL, "px and py must not both be null");
+    double t[3];
+    std::vector<unsigned> st;
+    rc = totals_range(c, lat, 1, t, st);
+    if (rc) return rc;
+    if (px) *px = t[1];
+    if (py) *py = t[2];
+    return status_code(st[lat]);
+}
+
+int lbm_totals_all(lbm_ctx* c, double* out) {
+    Range range("lbm_totals_all");
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (!out) return fail(LBM_EINVAL, "out must not be null");
+    std::vector<unsigned> st;
+    int rc = totals_range(c, 0, c->n, out, st);
+    if (rc) return rc;
+    unsigned all = 0;
+    for (unsigned s : st) all |= s;
+    return status_code(all);
 }
 
 int lbm_status(lbm_ctx* c, int lat, uint32_t* flags) {

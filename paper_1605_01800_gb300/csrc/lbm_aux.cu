@@ -1,5 +1,5 @@
 // Non-hot kernels of the library: initial state, macroscopic read-out and the
-// FP64 mass reduction. All arithmetic here is FP64.
+// FP64 mass and momentum reductions. All arithmetic here is FP64.
 #include "lbm_launch.h"
 
 namespace lbm {
@@ -260,6 +260,23 @@ __global__ void density_kernel(const Geom* __restrict__ geoms, const Phys<double
     }
 }
 
+// Force of Eq. 7 at the fluid node with cell index c and pseudopotential psi,
+// from a psi plane with a one-cell frame (negative psi marks a solid cell,
+// which takes the node's own psi).
+__device__ __forceinline__ void force_fp64(const Geom& g, const Phys<double>& P, const double* psi_plane, int c,
+                                           double psi, double& Fx, double& Fy) {
+    double gx = 0.0, gy = 0.0;
+    for (int a = 1; a < 9; ++a) {
+        double pn = psi_plane[c + kEy[a] * g.pitch + kEx[a]];
+        pn = pn < 0.0 ? psi : pn;
+        const double wa = (a < 5) ? (1.0 / 3.0) : (1.0 / 12.0);
+        gx += wa * pn * kEx[a];
+        gy += wa * pn * kEy[a];
+    }
+    Fx = -P.G * psi * gx;
+    Fy = -P.G * psi * gy;
+}
+
 // Read-out, pass 2: force (Eq. 7, a solid neighbour takes the node's psi),
 // velocity (Eq. 6) and pressure (Eq. 10) of every node; ux/uy hold the
 // momentum on entry and the velocity on exit.
@@ -283,15 +300,8 @@ __global__ void moments_force_kernel(const Geom* __restrict__ geoms, const Phys<
             p[o] = 0.0;
             continue;
         }
-        double gx = 0.0, gy = 0.0;
-        for (int a = 1; a < 9; ++a) {
-            double pn = psi_plane[c + kEy[a] * g.pitch + kEx[a]];
-            pn = pn < 0.0 ? psi : pn;
-            const double wa = (a < 5) ? (1.0 / 3.0) : (1.0 / 12.0);
-            gx += wa * pn * kEx[a];
-            gy += wa * pn * kEy[a];
-        }
-        const double Fx = -P.G * psi * gx, Fy = -P.G * psi * gy;
+        double Fx, Fy;
+        force_fp64(g, P, psi_plane, c, psi, Fx, Fy);
         const double r = rho[o];
         ux[o] = (ux[o] + 0.5 * Fx) / r;
         uy[o] = (uy[o] + 0.5 * Fy) / r;
@@ -326,11 +336,75 @@ __global__ void mass_partial_kernel(Geom g, const T* __restrict__ f, const uint8
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
+// Per-lattice totals after moments_psi_kernel (psi plane, j in jx/jy): block
+// b of lattice lat0 + blockIdx.y visits the fluid nodes i = b*T + t + k*B*T
+// and adds (0) the stored values, in the order of mass_partial_kernel, (1)
+// one per node, (2, 3) j + F/2, the numerator of Eq. 6; then the same fixed
+// tree as mass_partial_kernel. partials[((lat - lat0)*4 + q)*B + b].
+template <typename T>
+__global__ void totals_partial_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
+                                      int lat0, const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
+                                      const double* __restrict__ psi_base, const double* __restrict__ jx,
+                                      const double* __restrict__ jy, double* __restrict__ partials) {
+    __shared__ double red[4][kMassThreads];
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    const Phys<double> P = phys[lat];
+    const uint8_t* mask = geom_mask(g) ? mask_base + g.mask_off : nullptr;
+    const T* f = f_base + g.f_off;
+    const double* psi_plane = psi_base + g.f_off / 9;
+    const long long n = (long long)g.nx * g.ny;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)kMassThreads + threadIdx.x; i < n;
+         i += (long long)kMassBlocks * kMassThreads) {
+        const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+        if (is_solid(mask, g, x, y)) continue;
+        const long long c = node_index(g, x, y);
+        double s = 0.0;
+        for (int a = 0; a < 9; ++a) s += (double)f[a * g.plane + c];
+        acc[0] += s;
+        acc[1] += 1.0;
+        double Fx, Fy;
+        force_fp64(g, P, psi_plane, (int)c, psi_plane[c], Fx, Fy);
+        const long long o = g.node_off + i;
+        acc[2] += jx[o] + 0.5 * Fx;
+        acc[3] += jy[o] + 0.5 * Fy;
+    }
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kMassThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4)
+        partials[((long long)blockIdx.y * 4 + threadIdx.x) * kMassBlocks + blockIdx.x] = red[threadIdx.x][0];
+}
+
+// One thread per lattice: out[3k] = mass (the partial sums in block order
+// plus rho_ref times the fluid node count, as mass_final_kernel), out[3k + 1],
+// out[3k + 2] = the momentum sums.
+__global__ void totals_final_kernel(const double* __restrict__ partials, const Phys<double>* __restrict__ phys,
+                                    int lat0, int n_lat, double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_lat) return;
+    double s[4];
+    for (int q = 0; q < 4; ++q) {
+        const double* p = partials + ((long long)k * 4 + q) * kMassBlocks;
+        double t = 0.0;
+        for (int b = 0; b < kMassBlocks; ++b) t += p[b];
+        s[q] = t;
+    }
+    out[3 * k] = __fma_rn(phys[lat0 + k].rho_ref, s[1], s[0]);
+    out[3 * k + 1] = s[2];
+    out[3 * k + 2] = s[3];
+}
+
 __global__ void mass_final_kernel(const double* __restrict__ partials, double rho_ref,
                                   long long n_fluid, double* out) {
     double s = 0.0;
     for (int b = 0; b < kMassBlocks; ++b) s += partials[b];
-    *out = s + rho_ref * (double)n_fluid;
+    *out = __fma_rn(rho_ref, (double)n_fluid, s);
 }
 
 dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
@@ -389,6 +463,21 @@ cudaError_t density_impl(const LaunchSet& L, const T* f, double* rho, cudaStream
 }
 
 template <typename T>
+cudaError_t totals_impl(const LaunchSet& L, const T* f, double* psi, double* rho, double* jx, double* jy,
+                        double* partials, double* out, cudaStream_t s) {
+    moments_psi_kernel<T><<<lattice_grid(L.max_nodes + 2 * L.max_extent + 4, L.n_lat, 128), 128, 0, s>>>(
+        L.geoms, L.phys, L.lat0, f, L.mask, psi, rho, jx, jy);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    totals_partial_kernel<T><<<dim3(kMassBlocks, L.n_lat), kMassThreads, 0, s>>>(L.geoms, L.phys, L.lat0, f, L.mask,
+                                                                                psi, jx, jy, partials);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    totals_final_kernel<<<(L.n_lat + 127) / 128, 128, 0, s>>>(partials, L.phys, L.lat0, L.n_lat, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T* f,
                       const uint8_t* mask, double* partials, double* out, cudaStream_t s) {
     mass_partial_kernel<T><<<kMassBlocks, kMassThreads, 0, s>>>(g, f + g.f_off, mask, partials);
@@ -438,6 +527,14 @@ cudaError_t launch_moments_f32(const LaunchSet& L, const float* f, double* psi, 
 cudaError_t launch_moments_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* ux,
                                double* uy, double* p, cudaStream_t s) {
     return moments_impl<double>(L, f, psi, rho, ux, uy, p, s);
+}
+cudaError_t launch_totals_f32(const LaunchSet& L, const float* f, double* psi, double* rho, double* jx,
+                              double* jy, double* partials, double* out, cudaStream_t s) {
+    return totals_impl<float>(L, f, psi, rho, jx, jy, partials, out, s);
+}
+cudaError_t launch_totals_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* jx,
+                              double* jy, double* partials, double* out, cudaStream_t s) {
+    return totals_impl<double>(L, f, psi, rho, jx, jy, partials, out, s);
 }
 cudaError_t launch_mass_f32(const Geom& g, double rho_ref, long long n_fluid, const float* f,
                             const uint8_t* mask, double* partials, double* out, cudaStream_t s) {

@@ -154,4 +154,14 @@ cudaError_t launch_mass_f32(const Geom& g, double rho_ref, long long n_fluid, co
 cudaError_t launch_mass_f64(const Geom& g, double rho_ref, long long n_fluid, const double* f,
                             const uint8_t* mask, double* partials, double* out, cudaStream_t s);
 
+// Fixed-order FP64 totals of the lattices of L: out[3k .. 3k + 2] = mass (the
+// value launch_mass_* gives, bit for bit), sum of j_x + F_x/2, sum of j_y +
+// F_y/2 over the fluid nodes of lattice L.lat0 + k. psi, rho, jx, jy are the
+// read-out scratch of launch_moments_*; partials holds 4 * kMassBlocks
+// doubles per lattice.
+cudaError_t launch_totals_f32(const LaunchSet& L, const float* f, double* psi, double* rho, double* jx,
+                              double* jy, double* partials, double* out, cudaStream_t s);
+cudaError_t launch_totals_f64(const LaunchSet& L, const double* f, double* psi, double* rho, double* jx,
+                              double* jy, double* partials, double* out, cudaStream_t s);
+
 }  // namespace lbm

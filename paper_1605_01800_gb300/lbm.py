@@ -40,7 +40,7 @@ EXPORTED = [
     "lbm_clear_status", "lbm_sync", "lbm_state_size", "lbm_save_state", "lbm_load_state",
     "lbm_tile_count", "lbm_tile_shape", "lbm_tile_kind", "lbm_set_tile", "lbm_autotune", "lbm_info",
     "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc", "lbm_get_state_view",
-    "lbm_set_open_x", "lbm_halo_pack", "lbm_halo_unpack",
+    "lbm_set_open_x", "lbm_halo_pack", "lbm_halo_unpack", "lbm_total_momentum", "lbm_totals_all",
 ]
 
 
@@ -117,6 +117,8 @@ def load(build_if_missing: bool = True):
     lib.lbm_read_moments.argtypes = [_ctx, I, _dp, _dp, _dp, _dp]
     lib.lbm_read_moments_all.argtypes = [_ctx, _dp, _dp, _dp, _dp]
     lib.lbm_total_mass.argtypes = [_ctx, I, _dp]
+    lib.lbm_total_momentum.argtypes = [_ctx, I, _dp, _dp]
+    lib.lbm_totals_all.argtypes = [_ctx, _dp]
     lib.lbm_status.argtypes = [_ctx, I, ctypes.POINTER(ctypes.c_uint32)]
     lib.lbm_clear_status.argtypes = [_ctx]
     lib.lbm_sync.argtypes = [_ctx]
@@ -228,6 +230,22 @@ def lbm_total_mass(ctx, lat, allow_flags=False):
     allow = (LBM_EPSI_DOMAIN, LBM_ENONFINITE) if allow_flags else ()
     _check(load().lbm_total_mass(ctx, lat, ctypes.byref(m)), allow)
     return m.value
+
+
+def lbm_total_momentum(ctx, lat, allow_flags=False):
+    """(sum of rho v_x, sum of rho v_y) over the fluid nodes of lattice lat."""
+    px, py = ctypes.c_double(), ctypes.c_double()
+    allow = (LBM_EPSI_DOMAIN, LBM_ENONFINITE) if allow_flags else ()
+    _check(load().lbm_total_momentum(ctx, lat, ctypes.byref(px), ctypes.byref(py)), allow)
+    return px.value, py.value
+
+
+def lbm_totals_all(ctx, n_lattices, allow_flags=False):
+    """(n_lattices, 3) array: mass, momentum x, momentum y of every lattice."""
+    out = np.zeros((n_lattices, 3))
+    allow = (LBM_EPSI_DOMAIN, LBM_ENONFINITE) if allow_flags else ()
+    _check(load().lbm_totals_all(ctx, _ptr(out)), allow)
+    return out
 
 
 def lbm_status(ctx, lat):
@@ -395,6 +413,12 @@ class Batch:
 
     def mass(self, i, allow_flags=False):
         return lbm_total_mass(self.ctx, i, allow_flags=allow_flags)
+
+    def momentum(self, i, allow_flags=False):
+        return lbm_total_momentum(self.ctx, i, allow_flags=allow_flags)
+
+    def totals(self, allow_flags=False):
+        return lbm_totals_all(self.ctx, len(self.specs), allow_flags=allow_flags)
 
     def status(self, i):
         return lbm_status(self.ctx, i)

@@ -26,14 +26,15 @@ def _spec():
     return small_spec(96, 40, tr=0.6, walls=True, seed=271, shape="bubble", R=12.0)
 
 
-def _whole(spec, precision, steps):
+def _whole(spec, precision, steps, momentum=False):
     b = lbm.Batch([spec], precision)
     b.init()
     b.step(steps)
     out = b.moments(0)
     mass = b.mass(0)
+    mom = b.momentum(0)
     b.close()
-    return out, mass
+    return (out, mass, mom) if momentum else (out, mass)
 
 
 def _first_of(kind):
@@ -47,7 +48,7 @@ def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind):
     the slabs' interior tiles, the plain kernel's general path the tiles
     along the cuts)."""
     spec = _spec()
-    ref, mass = _whole(spec, precision, STEPS)
+    ref, mass, mom = _whole(spec, precision, STEPS, momentum=True)
     slabs = xslab.LocalSlabs(spec, [0, 37, 59, 96], precision)   # widths 37, 22, 37
     tile = 1 if kind == lbm.LBM_TILE_PLAIN else _first_of(kind)
     for s in slabs.slabs:
@@ -58,6 +59,9 @@ def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind):
         assert np.array_equal(a, b), name
     # the mass of the stored state adds up across the slabs
     assert sum(s.batch.mass(0) for s in slabs.slabs) == pytest.approx(mass, rel=1e-12)
+    # and so does the momentum, the force at the cut taken from the halo
+    for k in range(2):
+        assert sum(s.batch.momentum(0)[k] for s in slabs.slabs) == pytest.approx(mom[k], abs=1e-12 * mass)
     slabs.close()
 
 
