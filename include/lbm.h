@@ -58,6 +58,17 @@ extern "C" {
 #define LBM_FP32_DEV 0        /* FP32 storage and collision of f_a - w_a rho_ref */
 #define LBM_FP32 1            /* FP32 storage of f_a (rho_ref forced to 0) */
 #define LBM_FP64 2            /* FP64 storage and arithmetic */
+/* OR'ed into `precision`: in-place storage (the AA pattern), one
+ * distribution array instead of two (36 instead of 72 bytes per node in
+ * FP32), for lattices that would not fit otherwise. Streaming (Eq. 5) is
+ * folded into the stores of every other step, so the array alternates
+ * between two layouts (lbm_state_view.layout). A step is two launches, psi
+ * of every node into a scratch plane and then the collision in place, and
+ * moves 116 bytes per node instead of 72. Results are bitwise those of
+ * two-buffer storage. Not available with lbm_set_open_x; lbm_set_tile and
+ * lbm_autotune take the LBM_TILE_PLAIN shapes only (others: LBM_EINVAL or
+ * skipped). */
+#define LBM_INPLACE 0x100
 
 /* ---- sticky per-lattice status bits (lbm_status) ------------------------- */
 #define LBM_FLAG_PSI_CLAMPED 1u
@@ -134,6 +145,7 @@ typedef struct {
     int tile_x, tile_y;        /* node tile of one CTA of the step kernel */
     int n_tiles;               /* CTAs of one step launch */
     int graph_chunk;           /* steps per CUDA-graph replay in lbm_step */
+    int inplace;               /* 1 for in-place storage (LBM_INPLACE) */
 } lbm_info_t;
 
 /* Where one lattice's current state lives on the device (lbm_state_view),
@@ -146,7 +158,8 @@ typedef struct {
  * around the nodes (the other rows and columns of each plane) holds no
  * populations: no step reads it, so it may hold anything.
  * The view describes the buffer that the next step reads; a step writes
- * the other buffer and then reads from it, so query again after lbm_step.
+ * the other buffer and then reads from it (in place: the same array in the
+ * other layout), so query again after lbm_step.
  * The memory belongs to the context (valid until lbm_destroy), and access
  * is ordered with the context's stream by the caller (lbm_sync). */
 typedef struct {
@@ -158,6 +171,13 @@ typedef struct {
     int elem_bytes;      /* 4 (FP32 storage) or 8 (FP64) */
     int deviation;       /* 1 for FP32 deviation storage */
     double rho_ref;      /* the deviation reference (0 for plain storage) */
+    int layout;          /* what plane a at node x holds:
+                          *   0  two-buffer storage: f*_a(x), the post-collision
+                          *      value the next step pulls to x + e_a;
+                          *   1  in-place storage, natural layout: f_a(x), already
+                          *      streamed;
+                          *   2  in-place storage, swapped layout: f*_opp(a)(x),
+                          *      streaming pending (e_opp(a) = -e_a). */
 } lbm_state_view;
 
 /* Create a one-lattice context (the paper's single-domain runs, Sec. 3-4).

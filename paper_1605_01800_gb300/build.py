@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "liblbm.so")
 DEBUG_DIR = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(DEBUG_DIR, "liblbm.so")
 SOURCES = ["lbm_api.cu", "lbm_step_f32.cu", "lbm_step_f32_open.cu", "lbm_step_f64.cu", "lbm_step_tma.cu",
-           "lbm_step_pipe.cu", "lbm_aux.cu", "lbm_noalloc.cu"]
+           "lbm_step_pipe.cu", "lbm_step_inplace.cu", "lbm_aux.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -53,6 +53,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr double kCs2 = 1.0 / 3.0;
 constexpr int kGraphChunk = 32;  // steps per captured graph (even: parity is preserved)
 constexpr uint32_t kStateMagic = 0x4c424d31u;  // "LBM1"
+// blob kind word: the precision, LBM_INPLACE for in-place storage, and
+// kBlobSwapped when an in-place state was saved in the swapped layout
+constexpr uint32_t kBlobSwapped = 0x10000u;
 
 struct HostLattice {
     lbm_lattice_desc desc;       // wall_mask pointer not kept
@@ -85,6 +88,9 @@ struct lbm_ctx {
 
     void* f[2] = {nullptr, nullptr};
     int cur = 0;                 // buffer holding the state read by the next step
+    // in-place storage: one distribution array (f[1] == f[0]); cur is the
+    // layout of the state, 0 natural, 1 swapped (kLayoutNatural/Swapped)
+    bool inplace = false;
     uint8_t* d_mask = nullptr;
     Geom* d_geom = nullptr;
     Phys<float>* d_phys_f = nullptr;
@@ -253,7 +259,7 @@ void free_ctx(lbm_ctx* c) {
     if (!c) return;
     drop_graphs(c);
     cudaFree(c->f[0]);
-    cudaFree(c->f[1]);
+    if (c->f[1] != c->f[0]) cudaFree(c->f[1]);
     cudaFree(c->d_mask);
     cudaFree(c->d_geom);
     cudaFree(c->d_phys_f);
@@ -290,8 +296,15 @@ void tile_shape(int index, int* tx, int* ty) {
     }
 }
 
+// layout of the stored state (the step kernels' and read-outs' view of it)
+int state_layout(const lbm_ctx* c) {
+    if (!c->inplace) return kLayoutPull;
+    return c->cur == 0 ? kLayoutNatural : kLayoutSwapped;
+}
+
 // kernel launches of one step with the current tile list
 int launches_per_step(const lbm_ctx* c) {
+    if (c->inplace) return 2;
     if (is_pipe(c->tile_index)) return (c->n_fast > 0 ? 1 : 0) + (c->n_tiles > 0 ? 1 : 0);
     if (is_tma(c->tile_index)) return (c->n_tma > 0 ? 1 : 0) + (c->n_tiles > 0 ? 1 : 0);
     return 1;
@@ -345,6 +358,8 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     if (tile_index < 0 || tile_index >= total_tiles()) return fail(LBM_EINVAL, "no tile shape %d", tile_index);
     if (tile_index >= kTileCount && c->precision == LBM_FP64)
         return fail(LBM_EINVAL, "tile %d is an FP32-only variant; this context stores FP64", tile_index);
+    if (tile_index >= kTileCount && c->inplace)
+        return fail(LBM_EINVAL, "tile %d is a two-buffer variant; this context stores in place", tile_index);
     if (is_tma(tile_index) && c->n > kTmaMaxLattices)  // refused before the current tile list is replaced
         return fail(LBM_EINVAL, "tile %d (TMA) takes batches of at most %d lattices", tile_index, kTmaMaxLattices);
     const bool pipe = is_pipe(tile_index), tma = is_tma(tile_index);
@@ -538,11 +553,23 @@ LaunchSet launch_set(lbm_ctx* c, int lat0, int n_lat) {
         mx = std::max(mx, (long long)g.nx * g.ny);
         me = std::max(me, (long long)g.nx + g.ny);
     }
-    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx, me};
+    return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx, me, state_layout(c)};
 }
 
 cudaError_t launch_one_step(lbm_ctx* c, int src) {
     cudaError_t e;
+    if (c->inplace) {
+        int tx = 0, ty = 0;
+        tile_shape(c->tile_index, &tx, &ty);
+        const int layout = src == 0 ? kLayoutNatural : kLayoutSwapped;
+        if (c->precision == LBM_FP64)
+            e = launch_step_inplace_f64(c->d_tgeo, c->n_tiles, tx, ty, c->d_phys_d, (double*)c->f[0], c->d_mask,
+                                        c->d_psi, c->d_status, layout, c->stream);
+        else
+            e = launch_step_inplace_f32(c->d_tgeo, c->n_tiles, tx, ty, c->d_phys_f, (float*)c->f[0], c->d_mask,
+                                        (float*)c->d_psi, c->d_status, layout, c->stream);
+        return e;
+    }
     if (c->precision == LBM_FP64) {
         StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
                            (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
@@ -794,6 +821,8 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     *out = nullptr;
     if (n < 1 || !desc) return fail(LBM_EINVAL, "need n >= 1 lattice descriptions");
     if (n > 65535) return fail(LBM_EINVAL, "n=%d lattices: at most 65535 per context", n);
+    const bool inplace = (precision & LBM_INPLACE) != 0;
+    precision &= ~LBM_INPLACE;
     if (precision != LBM_FP32_DEV && precision != LBM_FP32 && precision != LBM_FP64)
         return fail(LBM_EINVAL, "unknown precision %d", precision);
     for (int i = 0; i < n; ++i) {
@@ -813,6 +842,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     if (const char* a = getenv("LBM_FAIL_ALLOC_AT")) c->fail_alloc_at = std::max(0LL, atoll(a));
     c->n = n;
     c->precision = precision;
+    c->inplace = inplace;
     c->elem = precision == LBM_FP64 ? 8 : 4;
     c->lats.resize(n);
     c->phys_d.resize(n);
@@ -864,7 +894,8 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     int rc = LBM_OK;
     const size_t fbytes = (size_t)c->total_elems * c->elem;
     if (!rc) rc = dev_alloc(c, &c->f[0], fbytes);
-    if (!rc) rc = dev_alloc(c, &c->f[1], fbytes);
+    if (!rc && !c->inplace) rc = dev_alloc(c, &c->f[1], fbytes);
+    if (!rc && c->inplace) c->f[1] = c->f[0];
     if (!rc && m_off > 0) rc = dev_alloc(c, &c->d_mask, (size_t)m_off);
     if (!rc) rc = dev_alloc(c, &c->d_geom, n * sizeof(Geom));
     if (!rc) rc = dev_alloc(c, &c->d_phys_f, n * sizeof(Phys<float>));
@@ -893,7 +924,7 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemset(c->f[0], 0, fbytes);
-    if (e == cudaSuccess) e = cudaMemset(c->f[1], 0, fbytes);
+    if (e == cudaSuccess && c->f[1] != c->f[0]) e = cudaMemset(c->f[1], 0, fbytes);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, n * sizeof(unsigned));
     if (e == cudaSuccess && m_off > 0) {
         e = cudaMemset(c->d_mask, 0, (size_t)m_off);
@@ -1039,10 +1070,12 @@ int lbm_total_mass(lbm_ctx* c, int lat, double* mass) {
     const uint8_t* dm = L.mask.empty() ? nullptr : c->d_mask + L.geom.mask_off;
     cudaError_t e;
     if (c->precision == LBM_FP64)
-        e = launch_mass_f64(L.geom, L.rho_ref, L.n_fluid, (const double*)c->f[c->cur], dm, c->d_partials,
+        e = launch_mass_f64(L.geom, L.rho_ref, L.n_fluid, (const double*)c->f[c->cur], dm, state_layout(c),
+                            c->d_partials,
                             c->d_scalar, c->stream);
     else
-        e = launch_mass_f32(L.geom, L.rho_ref, L.n_fluid, (const float*)c->f[c->cur], dm, c->d_partials,
+        e = launch_mass_f32(L.geom, L.rho_ref, L.n_fluid, (const float*)c->f[c->cur], dm, state_layout(c),
+                            c->d_partials,
                             c->d_scalar, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "mass kernels");
     c->launches += 2;
@@ -1137,6 +1170,12 @@ int lbm_state_size(lbm_ctx* c, size_t* bytes) {
 
 namespace {
 
+uint32_t blob_kind(const lbm_ctx* c) {
+    uint32_t k = (uint32_t)c->precision;
+    if (c->inplace) k |= (uint32_t)LBM_INPLACE | (c->cur ? kBlobSwapped : 0u);
+    return k;
+}
+
 // Copy every lattice's nodes between the device layout (frame, row
 // pitch `pitch`) and the compact checkpoint layout (plane a of lattice l at
 // c_off + a*ny*cpitch, node (x, y) at y*cpitch + x, cpitch = round_up(nx, 32)).
@@ -1168,7 +1207,7 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
     if (rc) return rc;
     if (!buf || bytes < need) return fail(LBM_EINVAL, "state buffer needs %zu bytes, got %zu", need, bytes);
     char* p = (char*)buf;
-    uint32_t hdr[4] = {kStateMagic, (uint32_t)c->precision, (uint32_t)c->n, (uint32_t)c->compact_elems};
+    uint32_t hdr[4] = {kStateMagic, blob_kind(c), (uint32_t)c->n, (uint32_t)c->compact_elems};
     memcpy(p, hdr, sizeof(hdr));
     p += sizeof(hdr);
     memcpy(p, &c->steps, sizeof(long long));
@@ -1194,7 +1233,8 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     uint32_t hdr[4];
     memcpy(hdr, p, sizeof(hdr));
     p += sizeof(hdr);
-    if (hdr[0] != kStateMagic || hdr[1] != (uint32_t)c->precision || hdr[2] != (uint32_t)c->n ||
+    const uint32_t kind = hdr[1] & ~kBlobSwapped;
+    if (hdr[0] != kStateMagic || kind != (blob_kind(c) & ~kBlobSwapped) || hdr[2] != (uint32_t)c->n ||
         hdr[3] != (uint32_t)c->compact_elems)
         return fail(LBM_EINVAL, "state blob does not match this context (lattices or precision differ)");
     long long steps;
@@ -1212,6 +1252,7 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     c->steps = steps;
+    if (c->inplace) c->cur = (hdr[1] & kBlobSwapped) ? 1 : 0;
     return LBM_OK;
 }
 
@@ -1284,8 +1325,9 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
         return cuda_fail(e, "autotune set-up");
     }
     for (int t = 0; t < total_tiles(); ++t) {
-        if ((t >= kTileCount && c->precision == LBM_FP64) || (is_tma(t) && c->n > kTmaMaxLattices)) {
-            if (ms) ms[t] = -1.0;  // FP32-only variant, or too many lattices for it
+        if ((t >= kTileCount && (c->precision == LBM_FP64 || c->inplace)) ||
+            (is_tma(t) && c->n > kTmaMaxLattices)) {
+            if (ms) ms[t] = -1.0;  // FP32 two-buffer variant, or too many lattices for it
             continue;
         }
         rc = build_tiles(c, t);
@@ -1357,6 +1399,7 @@ int lbm_get_state_view(lbm_ctx* c, int lat, lbm_state_view* view) {
     view->elem_bytes = c->elem;
     view->deviation = c->precision == LBM_FP32_DEV ? 1 : 0;
     view->rho_ref = c->precision == LBM_FP32_DEV ? L.rho_ref : 0.0;
+    view->layout = state_layout(c);
     return LBM_OK;
 }
 
@@ -1372,6 +1415,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     tile_shape(c->tile_index, &info->tile_x, &info->tile_y);
     info->n_tiles = c->n_tiles + c->n_fast + c->n_tma;
     info->graph_chunk = kGraphChunk;
+    info->inplace = c->inplace ? 1 : 0;
     return LBM_OK;
 }
 
@@ -1381,6 +1425,7 @@ int lbm_set_open_x(lbm_ctx* c, int lat, const uint8_t* halo_mask) {
     if (rc) return rc;
     HostLattice& L = c->lats[lat];
     Geom& g = L.geom;
+    if (c->inplace) return fail(LBM_EINVAL, "an x-slab needs two-buffer storage; this context stores in place");
     if (g.nx < 2) return fail(LBM_EINVAL, "lattice %d: an x-slab needs nx >= 2 (nx=%d)", lat, g.nx);
     if (c->precision == LBM_FP32_DEV && L.rho_ref_auto)
         return fail(LBM_EINVAL, "lattice %d: an x-slab needs an explicit rho_ref (>= 0) shared by every slab of "

@@ -31,12 +31,14 @@ __device__ __forceinline__ double feq(int a, double rho, double ux, double uy) {
 // w_b (rho - rho_ref). Invalid input (a fluid density that is not finite and
 // > 0, a non-finite velocity) sets bad[lat] = gen: `bad` is the host's
 // page-locked flag array, mapped, and gen identifies the host call, so the
-// flags need no clearing and no copy back.
+// flags need no clearing and no copy back. In-place storage: the swapped
+// layout keeps the same values in the opposite planes; the natural layout
+// holds f_eq of the node itself in its own planes.
 template <typename T>
 __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                             int lat0, const double* __restrict__ rho, const double* __restrict__ ux,
                             const double* __restrict__ uy, const uint8_t* __restrict__ mask_base,
-                            T* __restrict__ f_base, unsigned* __restrict__ bad, unsigned gen) {
+                            T* __restrict__ f_base, unsigned* __restrict__ bad, unsigned gen, int layout) {
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const double rho_ref = phys[lat].rho_ref;
@@ -59,16 +61,20 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
         if (!(isfinite(rho[i]) && rho[i] > 0.0)) invalid = 1;
         if ((ux && !isfinite(ux[i])) || (uy && !isfinite(uy[i]))) invalid = 1;
         for (int b = 0; b < 9; ++b) {
-            const int xt = wrap_index(x + kEx[b], g.nx), yt = wrap_index(y + kEy[b], g.ny);
-            const bool back = is_solid(mask, g, xt, yt);
-            const long long j = back ? i : (long long)yt * g.nx + xt;
-            const int bb = back ? kOpp[b] : b;
+            long long j = i;
+            int bb = b;
+            if (layout != kLayoutNatural) {
+                const int xt = wrap_index(x + kEx[b], g.nx), yt = wrap_index(y + kEy[b], g.ny);
+                const bool back = is_solid(mask, g, xt, yt);
+                j = back ? i : (long long)yt * g.nx + xt;
+                bb = back ? kOpp[b] : b;
+            }
             double v;
             if (ux == nullptr && uy == nullptr)
                 v = kWeq[bb] * (rho[j] - rho_ref);
             else
                 v = feq(bb, rho[j], ux ? ux[j] : 0.0, uy ? uy[j] : 0.0) - kWeq[bb] * rho_ref;
-            out[b] = (T)v;
+            out[layout == kLayoutSwapped ? kOpp[b] : b] = (T)v;
         }
         store_node<T>(f, g, x, y, out);
     }
@@ -174,10 +180,10 @@ __global__ void halo_unpack_kernel(Geom g, T* __restrict__ f_base, int side, con
 // their sum (the weights sum to 1) and the momentum their first moment (the
 // w_a rho_ref parts cancel), so the read-outs need no per-population FMA.
 template <typename T>
-__device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask, int x, int y,
-                                            double out[9]) {
+__device__ __forceinline__ bool pulled_fp64(const Geom& g, const T* f, const uint8_t* mask, int layout, int x,
+                                            int y, double out[9]) {
     T tmp[9];
-    if (pull_node<T>(f, mask, (int)g.plane, nbr_geom(g, x, y), tmp)) return false;
+    if (gather_node<T>(layout, f, mask, (int)g.plane, nbr_geom(g, x, y), tmp)) return false;
     for (int a = 0; a < 9; ++a) out[a] = (double)tmp[a];
     return true;
 }
@@ -196,7 +202,7 @@ template <typename T>
 __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                                    int lat0, const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
                                    double* __restrict__ psi_base, double* __restrict__ rho_out,
-                                   double* __restrict__ jx_out, double* __restrict__ jy_out) {
+                                   double* __restrict__ jx_out, double* __restrict__ jy_out, int layout) {
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const Phys<double> P = phys[lat];
@@ -209,7 +215,7 @@ __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<do
         const int x = (int)(i % w) - 1, y = (int)(i / w) - 1;
         double fc[9];
         const int c = node_index(g, x, y);
-        if (!pulled_fp64<T>(g, f, mask, x, y, fc)) {
+        if (!pulled_fp64<T>(g, f, mask, layout, x, y, fc)) {
             psi_plane[c] = -1.0;
             if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
                 const long long o = g.node_off + (long long)y * g.nx + x;
@@ -241,7 +247,7 @@ __global__ void moments_psi_kernel(const Geom* __restrict__ geoms, const Phys<do
 template <typename T>
 __global__ void density_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys, int lat0,
                                const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
-                               double* __restrict__ rho_out) {
+                               double* __restrict__ rho_out, int layout) {
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
     const double rho_ref = phys[lat].rho_ref;
@@ -252,7 +258,7 @@ __global__ void density_kernel(const Geom* __restrict__ geoms, const Phys<double
         const int y = i / g.nx, x = i - y * g.nx;
         double fc[9];
         double rho = 0.0;
-        if (pulled_fp64<T>(g, f, mask, x, y, fc)) {
+        if (pulled_fp64<T>(g, f, mask, layout, x, y, fc)) {
             rho = rho_ref;
             for (int a = 0; a < 9; ++a) rho += fc[a];
         }
@@ -310,11 +316,13 @@ __global__ void moments_force_kernel(const Geom* __restrict__ geoms, const Phys<
     }
 }
 
-// Partial sums: block b adds the stored values of the fluid nodes i = b*T + t
-// + k*B*T in a fixed order, then a fixed tree inside the block.
+// Partial sums: block b adds the post-collision values of the fluid nodes
+// i = b*T + t + k*B*T (the stored values of two-buffer storage; in-place
+// storage finds them by the layout) in a fixed order, then a fixed tree
+// inside the block.
 template <typename T>
 __global__ void mass_partial_kernel(Geom g, const T* __restrict__ f, const uint8_t* __restrict__ mask,
-                                    double* __restrict__ partials) {
+                                    int layout, double* __restrict__ partials) {
     __shared__ double red[kMassThreads];
     const long long n = (long long)g.nx * g.ny;
     double acc = 0.0;
@@ -322,9 +330,10 @@ __global__ void mass_partial_kernel(Geom g, const T* __restrict__ f, const uint8
          i += (long long)kMassBlocks * kMassThreads) {
         const int x = (int)(i % g.nx), y = (int)(i / g.nx);
         if (is_solid(mask, g, x, y)) continue;
-        const long long c = node_index(g, x, y);
+        T fs[9];
+        post_collision_node<T>(layout, f, mask, (int)g.plane, nbr_of(g.nx, g.ny, g.pitch, x, y), fs);
         double s = 0.0;
-        for (int a = 0; a < 9; ++a) s += (double)f[a * g.plane + c];
+        for (int a = 0; a < 9; ++a) s += (double)fs[a];
         acc += s;
     }
     red[threadIdx.x] = acc;
@@ -345,7 +354,7 @@ template <typename T>
 __global__ void totals_partial_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                                       int lat0, const T* __restrict__ f_base, const uint8_t* __restrict__ mask_base,
                                       const double* __restrict__ psi_base, const double* __restrict__ jx,
-                                      const double* __restrict__ jy, double* __restrict__ partials) {
+                                      const double* __restrict__ jy, int layout, double* __restrict__ partials) {
     __shared__ double red[4][kMassThreads];
     const int lat = lat0 + blockIdx.y;
     const Geom g = geoms[lat];
@@ -360,8 +369,10 @@ __global__ void totals_partial_kernel(const Geom* __restrict__ geoms, const Phys
         const int x = (int)(i % g.nx), y = (int)(i / g.nx);
         if (is_solid(mask, g, x, y)) continue;
         const long long c = node_index(g, x, y);
+        T fs[9];
+        post_collision_node<T>(layout, f, mask, (int)g.plane, nbr_of(g.nx, g.ny, g.pitch, x, y), fs);
         double s = 0.0;
-        for (int a = 0; a < 9; ++a) s += (double)f[a * g.plane + c];
+        for (int a = 0; a < 9; ++a) s += (double)fs[a];
         acc[0] += s;
         acc[1] += 1.0;
         double Fx, Fy;
@@ -418,7 +429,7 @@ template <typename T>
 cudaError_t init_impl(const LaunchSet& L, const double* rho, const double* ux, const double* uy,
                       T* f, unsigned* bad, unsigned gen, cudaStream_t s) {
     init_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(
-        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad, gen);
+        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad, gen, L.layout);
     return cudaGetLastError();
 }
 
@@ -447,7 +458,7 @@ cudaError_t moments_impl(const LaunchSet& L, const T* f, double* psi, double* rh
                          double* p, cudaStream_t s) {
     // cells of the nodes plus a one-cell frame: (nx + 2)(ny + 2) <= nodes + 2(nx + ny) + 4
     moments_psi_kernel<T><<<lattice_grid(L.max_nodes + 2 * L.max_extent + 4, L.n_lat, 128), 128, 0, s>>>(
-        L.geoms, L.phys, L.lat0, f, L.mask, psi, rho, ux, uy);
+        L.geoms, L.phys, L.lat0, f, L.mask, psi, rho, ux, uy, L.layout);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     moments_force_kernel<<<lattice_grid(L.max_nodes, L.n_lat, 128), 128, 0, s>>>(L.geoms, L.phys, L.lat0, psi,
@@ -458,7 +469,7 @@ cudaError_t moments_impl(const LaunchSet& L, const T* f, double* psi, double* rh
 template <typename T>
 cudaError_t density_impl(const LaunchSet& L, const T* f, double* rho, cudaStream_t s) {
     density_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(L.geoms, L.phys, L.lat0, f, L.mask,
-                                                                               rho);
+                                                                               rho, L.layout);
     return cudaGetLastError();
 }
 
@@ -466,11 +477,11 @@ template <typename T>
 cudaError_t totals_impl(const LaunchSet& L, const T* f, double* psi, double* rho, double* jx, double* jy,
                         double* partials, double* out, cudaStream_t s) {
     moments_psi_kernel<T><<<lattice_grid(L.max_nodes + 2 * L.max_extent + 4, L.n_lat, 128), 128, 0, s>>>(
-        L.geoms, L.phys, L.lat0, f, L.mask, psi, rho, jx, jy);
+        L.geoms, L.phys, L.lat0, f, L.mask, psi, rho, jx, jy, L.layout);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     totals_partial_kernel<T><<<dim3(kMassBlocks, L.n_lat), kMassThreads, 0, s>>>(L.geoms, L.phys, L.lat0, f, L.mask,
-                                                                                psi, jx, jy, partials);
+                                                                                psi, jx, jy, L.layout, partials);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     totals_final_kernel<<<(L.n_lat + 127) / 128, 128, 0, s>>>(partials, L.phys, L.lat0, L.n_lat, out);
@@ -479,8 +490,8 @@ cudaError_t totals_impl(const LaunchSet& L, const T* f, double* psi, double* rho
 
 template <typename T>
 cudaError_t mass_impl(const Geom& g, double rho_ref, long long n_fluid, const T* f,
-                      const uint8_t* mask, double* partials, double* out, cudaStream_t s) {
-    mass_partial_kernel<T><<<kMassBlocks, kMassThreads, 0, s>>>(g, f + g.f_off, mask, partials);
+                      const uint8_t* mask, int layout, double* partials, double* out, cudaStream_t s) {
+    mass_partial_kernel<T><<<kMassBlocks, kMassThreads, 0, s>>>(g, f + g.f_off, mask, layout, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     mass_final_kernel<<<1, 1, 0, s>>>(partials, rho_ref, n_fluid, out);
@@ -537,12 +548,12 @@ cudaError_t launch_totals_f64(const LaunchSet& L, const double* f, double* psi, 
     return totals_impl<double>(L, f, psi, rho, jx, jy, partials, out, s);
 }
 cudaError_t launch_mass_f32(const Geom& g, double rho_ref, long long n_fluid, const float* f,
-                            const uint8_t* mask, double* partials, double* out, cudaStream_t s) {
-    return mass_impl<float>(g, rho_ref, n_fluid, f, mask, partials, out, s);
+                            const uint8_t* mask, int layout, double* partials, double* out, cudaStream_t s) {
+    return mass_impl<float>(g, rho_ref, n_fluid, f, mask, layout, partials, out, s);
 }
 cudaError_t launch_mass_f64(const Geom& g, double rho_ref, long long n_fluid, const double* f,
-                            const uint8_t* mask, double* partials, double* out, cudaStream_t s) {
-    return mass_impl<double>(g, rho_ref, n_fluid, f, mask, partials, out, s);
+                            const uint8_t* mask, int layout, double* partials, double* out, cudaStream_t s) {
+    return mass_impl<double>(g, rho_ref, n_fluid, f, mask, layout, partials, out, s);
 }
 
 }  // namespace lbm

@@ -202,16 +202,38 @@ __device__ __forceinline__ uint8_t ld_mask(const uint8_t* __restrict__ m, int i,
     return m[i];
 }
 
+// Opposite velocity: e_opp(a) = -e_a.
+__host__ __device__ constexpr int opp(int a) {
+    return a == 0 ? 0 : (a < 5 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
+}
+
+// Layouts of a stored state. Two-buffer storage (kLayoutPull) keeps the
+// post-collision values of the last step, f*_a(x) in plane a at x, and the
+// next step pulls them. In-place storage (one array, the AA pattern)
+// alternates between two layouts:
+//   kLayoutNatural  plane a at x holds f_a(x), already streamed;
+//   kLayoutSwapped  plane opp(a) at x holds f*_a(x), streaming pending.
+// A step from the natural layout collides every node in place and writes
+// f*_a to plane opp(a) of the same node (swapped layout); a step from the
+// swapped layout gathers f_a(x) from plane opp(a) at x - e_a (plane a at x
+// when x - e_a is solid) and writes f*_a to plane a at x + e_a (plane
+// opp(a) at x when x + e_a is solid), which is the natural layout again.
+// Each node reads and writes only slots no other node touches in that step.
+constexpr int kLayoutPull = 0;
+constexpr int kLayoutNatural = 1;
+constexpr int kLayoutSwapped = 2;
+
 // Gather the distribution of node n after streaming (Eq. 5) from the
 // post-collision array `fin` (pull form): f_a(x) = f*_a(x - e_a), with x - e_a
 // taken periodically. With a wall mask, a link whose source is solid is
 // reflected: f_a(x) = f*_abar(x). Returns true if the node itself is solid
-// (then f is not filled).
-template <typename T>
+// (then f is not filled). SWAP reads f*_a from plane opp(a) instead of
+// plane a (the swapped layout of in-place storage).
+template <typename T, bool SWAP = false>
 __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8_t* __restrict__ mask,
                                           int plane, const Nbr& n, T f[9]) {
     const int np = 9 * plane;  // < 2^31 (checked when the lattice is created)
-    auto F = [&](int a, int i) { return ld_pop<T>(fin, a * plane + i, np); };
+    auto F = [&](int a, int i) { return ld_pop<T>(fin, (SWAP ? opp(a) : a) * plane + i, np); };
     const int c = n.c;
     if (mask != nullptr) {
         auto M = [&](int i) { return ld_mask(mask, i, plane); };
@@ -237,6 +259,62 @@ __device__ __forceinline__ bool pull_node(const T* __restrict__ fin, const uint8
     f[7] = F(7, c + n.yp + n.xp);
     f[8] = F(8, c + n.yp + n.xm);
     return false;
+}
+
+// The distribution of node n in any layout (see kLayoutPull): the pull of
+// two-buffer storage, the node's own planes (natural layout) or the pull
+// from the opposite planes (swapped layout). Returns true if the node is
+// solid.
+template <typename T>
+__device__ __forceinline__ bool gather_node(int layout, const T* __restrict__ f, const uint8_t* __restrict__ mask,
+                                            int plane, const Nbr& n, T out[9]) {
+    if (layout == kLayoutNatural) {
+        if (mask != nullptr && ld_mask(mask, n.c, plane)) return true;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) out[a] = ld_pop<T>(f, a * plane + n.c, 9 * plane);
+        return false;
+    }
+    return layout == kLayoutSwapped ? pull_node<T, true>(f, mask, plane, n, out)
+                                    : pull_node<T, false>(f, mask, plane, n, out);
+}
+
+// Offset from a node to its neighbour x + e_a (a = 1 .. 8) on the periodic
+// lattice, from the node's Nbr.
+__device__ __forceinline__ int nbr_offset(const Nbr& n, int a) {
+    switch (a) {
+        case 1: return n.xp;
+        case 2: return n.yp;
+        case 3: return n.xm;
+        case 4: return n.ym;
+        case 5: return n.yp + n.xp;
+        case 6: return n.yp + n.xm;
+        case 7: return n.ym + n.xm;
+        default: return n.ym + n.xp;
+    }
+}
+
+// The post-collision values f*_a of node n (the values the last step
+// wrote for it) in any layout: plane a at the node (two-buffer storage),
+// plane opp(a) at the node (swapped), or where streaming put them (natural:
+// plane a at x + e_a, plane opp(a) at the node when x + e_a is solid).
+template <typename T>
+__device__ __forceinline__ void post_collision_node(int layout, const T* __restrict__ f,
+                                                    const uint8_t* __restrict__ mask, int plane, const Nbr& n,
+                                                    T out[9]) {
+    const int np = 9 * plane;
+    for (int a = 0; a < 9; ++a) {
+        int slot = a, i = n.c;
+        if (layout == kLayoutSwapped) {
+            slot = opp(a);
+        } else if (layout == kLayoutNatural && a > 0) {
+            const int t = n.c + nbr_offset(n, a);
+            if (mask != nullptr && ld_mask(mask, t, plane))
+                slot = opp(a);
+            else
+                i = t;
+        }
+        out[a] = ld_pop<T>(f, slot * plane + i, np);
+    }
 }
 
 // pull_node for a node at stored index c whose eight neighbours all lie

@@ -106,7 +106,20 @@ struct LaunchSet {
     int lat0, n_lat;
     long long max_nodes;        // largest nx*ny among the lattices
     long long max_extent;       // largest nx + ny among the lattices
+    int layout;                 // layout of the stored state (kLayoutPull, kLayoutNatural, kLayoutSwapped)
 };
+
+// Step of in-place storage: two launches over the plain kernel's tile list
+// (tx x ty node tiles), psi of every node into `psi` (a plane per lattice in
+// the stored layout, at f_off / 9, with a one-cell periodic frame), then the
+// collision from `layout` (kLayoutNatural or kLayoutSwapped) into the other
+// layout, in place.
+cudaError_t launch_step_inplace_f32(const TileGeom* tg, int n_tiles, int tx, int ty, const Phys<float>* phys,
+                                    float* f, const uint8_t* mask, float* psi, unsigned* status, int layout,
+                                    cudaStream_t s);
+cudaError_t launch_step_inplace_f64(const TileGeom* tg, int n_tiles, int tx, int ty, const Phys<double>* phys,
+                                    double* f, const uint8_t* mask, double* psi, unsigned* status, int layout,
+                                    cudaStream_t s);
 
 // Initial state: f_a such that the next pull gathers f_eq(rho, u) at every
 // fluid node. rho/ux/uy are device arrays indexed by geom.node_off + y*nx + x
@@ -150,9 +163,9 @@ cudaError_t launch_density_f64(const LaunchSet& L, const double* f, double* rho,
 constexpr int kMassBlocks = 120;
 constexpr int kMassThreads = 256;
 cudaError_t launch_mass_f32(const Geom& g, double rho_ref, long long n_fluid, const float* f,
-                            const uint8_t* mask, double* partials, double* out, cudaStream_t s);
+                            const uint8_t* mask, int layout, double* partials, double* out, cudaStream_t s);
 cudaError_t launch_mass_f64(const Geom& g, double rho_ref, long long n_fluid, const double* f,
-                            const uint8_t* mask, double* partials, double* out, cudaStream_t s);
+                            const uint8_t* mask, int layout, double* partials, double* out, cudaStream_t s);
 
 // Fixed-order FP64 totals of the lattices of L: out[3k .. 3k + 2] = mass (the
 // value launch_mass_* gives, bit for bit), sum of j_x + F_x/2, sum of j_y +

@@ -27,12 +27,15 @@ LBM_ETIMEOUT = 6
 LBM_FP32_DEV = 0
 LBM_FP32 = 1
 LBM_FP64 = 2
+LBM_INPLACE = 0x100   # OR'ed into a precision: one distribution array (lbm.h)
 
 LBM_FLAG_PSI_CLAMPED = 1
 LBM_FLAG_NONFINITE = 2
 LBM_FLAG_TIMEOUT = 4
 
-PRECISIONS = {"fp32_dev": LBM_FP32_DEV, "fp32": LBM_FP32, "fp64": LBM_FP64}
+PRECISIONS = {"fp32_dev": LBM_FP32_DEV, "fp32": LBM_FP32, "fp64": LBM_FP64,
+              "fp32_dev_inplace": LBM_FP32_DEV | LBM_INPLACE, "fp32_inplace": LBM_FP32 | LBM_INPLACE,
+              "fp64_inplace": LBM_FP64 | LBM_INPLACE}
 
 EXPORTED = [
     "lbm_create", "lbm_create_batch", "lbm_set_stream", "lbm_init_fields", "lbm_init_fields_all",
@@ -71,13 +74,14 @@ class lbm_info_t(ctypes.Structure):
                 ("nodes", ctypes.c_longlong), ("fluid_nodes", ctypes.c_longlong),
                 ("steps", ctypes.c_longlong), ("kernel_launches", ctypes.c_ulonglong),
                 ("device_bytes", ctypes.c_size_t), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("n_tiles", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
+                ("n_tiles", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("inplace", ctypes.c_int)]
 
 
 class lbm_state_view(ctypes.Structure):
     _fields_ = [("base", ctypes.c_void_p), ("plane", ctypes.c_longlong), ("pitch", ctypes.c_int),
                 ("rows", ctypes.c_int), ("x0", ctypes.c_int), ("y0", ctypes.c_int),
-                ("elem_bytes", ctypes.c_int), ("deviation", ctypes.c_int), ("rho_ref", ctypes.c_double)]
+                ("elem_bytes", ctypes.c_int), ("deviation", ctypes.c_int), ("rho_ref", ctypes.c_double),
+                ("layout", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -69,6 +69,20 @@ def test_create_rejects_bad_parameters(kw, fragment):
     assert fragment in str(e.value)
 
 
+def test_precision_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    for name in ("LBM_FP32_DEV", "LBM_FP32", "LBM_FP64", "LBM_INPLACE"):
+        m = re.search(r"#define " + name + r"\s+(0x[0-9a-fA-F]+|\d+)", text)
+        assert m and int(m.group(1), 0) == getattr(lbm, name), name
+
+
+def test_create_rejects_an_unknown_precision():
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create_batch([_desc()], 3 | lbm.LBM_INPLACE)
+    assert e.value.code == lbm.LBM_EINVAL
+    assert "precision" in str(e.value)
+
+
 def test_create_rejects_an_empty_batch():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create_batch([], lbm.LBM_FP32_DEV)
