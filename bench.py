@@ -38,16 +38,21 @@ sys.path.insert(0, ROOT)
 
 ALG_BYTES_FP32 = 72   # 9 reads + 9 writes of 4 B per node update
 ALG_BYTES_FP64 = 144
+# in-place storage: psi pass (9 reads, 1 psi write) + collision (9 reads, the
+# node's psi, 9 writes; the neighbours' psi come from L1/L2), 4 B each
+ALG_BYTES_INPLACE = 116
 WORKLOAD = "coexistence_batch"
 PROFILE = os.path.join(ROOT, "profiles", "step_fp32_coexistence_batch.md")
 # ncu DRAM bytes of one step of the sustained workloads (same summary format)
 SUSTAINED_PROFILES = {"roofline_4096": os.path.join(ROOT, "profiles", "step_fp32_roofline_4096.md")}
+INPLACE_PROFILE = os.path.join(ROOT, "profiles", "step_fp32_inplace_roofline_4096.md")
 SUSTAINED = ("laplace_batch", "collapse_2048x1024", "roofline_4096", "collapse_x8")
 # device sources of each step-kernel kind whose ncu traffic the profile records
 # (a pipelined step also launches the plain kernel on its other tiles)
 _PLAIN = ("lbm_step.cuh", "lbm_device.cuh", "lbm_step_f32.cu", "lbm_step_f32.inc")
 KERNEL_SOURCES = {kind: [os.path.join(ROOT, "paper_1605_01800_gb300", "csrc", f) for f in files]
-                  for kind, files in (("plain", _PLAIN), ("pipelined", _PLAIN + ("lbm_step_pipe.cu",)))}
+                  for kind, files in (("plain", _PLAIN), ("pipelined", _PLAIN + ("lbm_step_pipe.cu",)),
+                                      ("inplace", ("lbm_device.cuh", "lbm_step_inplace.cu")))}
 
 
 def parse_args():
@@ -62,6 +67,7 @@ def parse_args():
                     help="profiling mode for ncu: only init and --steps FP32 steps of WORKLOAD "
                          "(coexistence_batch, laplace_batch, collapse_2048x1024, ...) with --tile")
     ap.add_argument("--tile", type=int, default=None, help="step-kernel tile index for --profile")
+    ap.add_argument("--precision", default="fp32_dev", help="storage for --profile (fp32_dev, fp32_dev_inplace, ...)")
     return ap.parse_args()
 
 
@@ -71,14 +77,15 @@ def run_profile(args):
     from paper_1605_01800_gb300 import inputs, lbm
     torch.cuda.set_device(0)
     specs = inputs.WORKLOADS[args.profile]()
-    b = lbm.Batch(specs, "fp32_dev")
+    b = lbm.Batch(specs, args.precision)
     if args.tile is not None:
         lbm.lbm_set_tile(b.ctx, args.tile)
     b.init()
     b.step(args.steps)
     lbm.lbm_sync(b.ctx)
     info = b.info()
-    print(json.dumps({"profile": args.profile, "tile_index": args.tile, "tile": [info["tile_x"], info["tile_y"]],
+    print(json.dumps({"profile": args.profile, "precision": args.precision, "tile_index": args.tile,
+                      "tile": [info["tile_x"], info["tile_y"]],
                       "steps": args.steps, "nodes": info["nodes"], "launches": info["kernel_launches"]}))
     b.close()
 
@@ -284,12 +291,12 @@ def timed_steps(torch, ctx, lbm, stream, flush, steps):
     return [e0.elapsed_time(e1) for e0, e1 in ev]
 
 
-def sustained_steps(torch, lbm, specs, stream, tiles, steps=256, warm=32):
+def sustained_steps(torch, lbm, specs, stream, tiles, steps=256, warm=32, precision="fp32_dev"):
     """Back-to-back steps of one batch on its own, no flush: CUDA-graph replay
     of `steps` steps with CUDA events around the whole replay, for the fastest
     of `tiles` (each tried on 64 steps from a fresh state). Returns
     (ms per step, tile index, {tile: ms per step of the trial})."""
-    b = lbm.Batch(specs, "fp32_dev", stream=stream)
+    b = lbm.Batch(specs, precision, stream=stream)
 
     def replay(n):
         with torch.cuda.stream(stream):
@@ -419,6 +426,22 @@ def main():
             entry["dram_bytes_per_node"] = None if tr is None else tr / lnodes
         sustained[name] = entry
         del lspecs
+
+    # ---- in-place storage on the 4096^2 lattice (one distribution array)
+    ispecs = inputs.WORKLOADS["roofline_4096"]()
+    inodes = sum(s.nodes for s in ispecs)
+    ims, it, itrial = sustained_steps(torch, lbm, ispecs, stream, plain, precision="fp32_dev_inplace")
+    igbs = ALG_BYTES_INPLACE * inodes / (ims * 1e-3) / 1e9
+    inplace = {"workload": "roofline_4096", "nodes": inodes, "distribution_bytes": 36 * inodes,
+               "tile": lbm.lbm_tile_shape(it), "tile_index": it, "steps": 256, "ms_per_step": ims,
+               "MLUPS": inodes / (ims * 1e-3) / 1e6, "alg_bytes_per_node": ALG_BYTES_INPLACE,
+               "achieved_gbs": igbs, "frac": igbs / peak,
+               "vs_two_buffers": sustained["roofline_4096"]["ms_per_step"] / ims,
+               "dram_bytes_per_node": (lambda tr: None if tr is None else tr / inodes)(
+                   profiled_traffic(it, "inplace", INPLACE_PROFILE)),
+               "tile_trial_us": {str(t): round(1e3 * v, 2) for t, v in itrial.items()},
+               "note": "LBM_INPLACE: one array, psi pass + in-place collision per step, CUDA-graph replay"}
+    del ispecs
     clk = clocks.stop()
 
     # ---- the Laplace batch split across the ranks by node count (strong
@@ -545,6 +568,7 @@ def main():
                      "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_node": ALG_BYTES_FP32},
         "sustained": dict(sustained, note="back-to-back steps, CUDA-graph replay of 256 steps, events around "
                                           "the replay, no flush; working sets larger than L2 (129 MB)"),
+        "inplace": inplace,
         "copy_same_bytes": {"achieved_gbs": copy_gbs, "ms": copy_ms, "frac": copy_gbs / peak,
                             "note": "torch device copy of 9 x 4 B per node, same flush"},
         "fp32_vs_fp64": acc,
