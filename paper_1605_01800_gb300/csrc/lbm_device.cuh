@@ -124,26 +124,33 @@ __device__ __forceinline__ Nbr nbr_geom(const Geom& g, int x, int y) {
 // Near the density where psi^2 = 0 the bracket cancels; the FP32 version
 // (vpsi below) recomputes it in FP64 there. psi^2 < 0 is clamped to 0 and
 // flagged.
+// The EOS helpers below spell every operation as an explicitly rounded
+// intrinsic, so that no multiply-add is contracted differently in the
+// kernels that inline them: every step kernel then computes bitwise the same
+// psi.
 __device__ __forceinline__ double psi_bracket_fp64(double rho, double RT, double a,
                                                    double b4, double cs2) {
-    double eta = b4 * rho;
-    double om = 1.0 - eta;
-    double num = 1.0 + eta * (1.0 + eta * (1.0 - eta));
-    return RT * (num / (om * om * om)) - a * rho - cs2;
+    const double eta = __dmul_rn(b4, rho);
+    const double om = __dsub_rn(1.0, eta);
+    const double num = __dadd_rn(1.0, __dmul_rn(eta, __dadd_rn(1.0, __dmul_rn(eta, __dsub_rn(1.0, eta)))));
+    const double z = __ddiv_rn(num, __dmul_rn(__dmul_rn(om, om), om));
+    return __dsub_rn(__dsub_rn(__dmul_rn(RT, z), __dmul_rn(a, rho)), cs2);
 }
 
 // p / rho - c_s^2 of the van der Waals (d = 1) or Peng-Robinson EOS, with
 // om = 1 - b rho (the pole at b rho = 1) and a the attraction (a alpha for PR).
 __device__ __forceinline__ double bracket_cubic_fp64(double rho, double RT, double a, double b, double cs2,
                                                      bool pr) {
-    const double om = 1.0 - b * rho;
-    const double att = pr ? a * rho / (1.0 + b * rho * (2.0 - b * rho)) : a * rho;
-    return RT / om - att - cs2;
+    const double br = __dmul_rn(b, rho);
+    const double om = __dsub_rn(1.0, br);
+    const double att = pr ? __ddiv_rn(__dmul_rn(a, rho), __dadd_rn(1.0, __dmul_rn(br, __dsub_rn(2.0, br))))
+                          : __dmul_rn(a, rho);
+    return __dsub_rn(__dsub_rn(__ddiv_rn(RT, om), att), cs2);
 }
 
 // psi of Eq. 12: exp(-1/rho) (eps = 0) or (rho / (eps + rho))^(1/eps).
 __device__ __forceinline__ double psi_exp_fp64(double rho, double eps, double inv_eps) {
-    return eps == 0.0 ? exp(-1.0 / rho) : exp(log(rho / (eps + rho)) * inv_eps);
+    return eps == 0.0 ? exp(__ddiv_rn(-1.0, rho)) : exp(__dmul_rn(log(__ddiv_rn(rho, __dadd_rn(eps, rho))), inv_eps));
 }
 
 __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsigned& flag) {
@@ -157,8 +164,8 @@ __device__ __forceinline__ double psi_of(double rho, const Phys<double>& P, unsi
     const bool cubic = P.eos != EOS_CS;
     double q = cubic ? bracket_cubic_fp64(rho, P.RT, P.a, P.b1, P.cs2, P.eos == EOS_PR)
                      : psi_bracket_fp64(rho, P.RT, P.a, P.b4, P.cs2);
-    double psi2 = P.kpsi * rho * q;
-    const bool dense_ok = (cubic ? 1.0 - P.b1 * rho : 1.0 - P.b4 * rho) > 0.0;
+    double psi2 = __dmul_rn(__dmul_rn(P.kpsi, rho), q);
+    const bool dense_ok = __dsub_rn(1.0, __dmul_rn(cubic ? P.b1 : P.b4, rho)) > 0.0;
     if (!(psi2 >= 0.0 && dense_ok)) {
         flag |= (psi2 < 0.0 && dense_ok) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
         psi2 = 0.0;
@@ -550,16 +557,20 @@ __device__ __forceinline__ float psi_variant(float rho, const Phys<float>& P, un
             flag |= FLAG_NONFINITE;
             return 0.0f;
         }
-        return P.eps12 == 0.0f ? expf(-1.0f / rho) : expf(logf(rho / (P.eps12 + rho)) * P.inv_eps12);
+        return P.eps12 == 0.0f ? expf(__fdiv_rn(-1.0f, rho))
+                               : expf(__fmul_rn(logf(__fdiv_rn(rho, __fadd_rn(P.eps12, rho))), P.inv_eps12));
     }
     const bool pr = P.eos == EOS_PR;
-    const float om = 1.0f - P.b1 * rho;
-    const float att = pr ? P.a * rho / fmaf(P.b1 * rho, 2.0f - P.b1 * rho, 1.0f) : P.a * rho;
-    const float q = P.RT / om - att - P.cs2;
-    float p2 = P.kpsi * rho * q;
+    const float br = __fmul_rn(P.b1, rho);
+    const float om = __fsub_rn(1.0f, br);
+    const float att = pr ? __fdiv_rn(__fmul_rn(P.a, rho), __fmaf_rn(br, __fsub_rn(2.0f, br), 1.0f))
+                         : __fmul_rn(P.a, rho);
+    const float q = __fsub_rn(__fsub_rn(__fdiv_rn(P.RT, om), att), P.cs2);
+    float p2 = __fmul_rn(__fmul_rn(P.kpsi, rho), q);
     if (fabsf(q) < 0.0078125f * P.cs2)
-        p2 = (float)((double)P.kpsi * (double)rho *
-                     bracket_cubic_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b1, (double)P.cs2, pr));
+        p2 = (float)__dmul_rn(__dmul_rn((double)P.kpsi, (double)rho),
+                              bracket_cubic_fp64((double)rho, (double)P.RT, (double)P.a, (double)P.b1,
+                                                 (double)P.cs2, pr));
     if (!(p2 >= 0.0f && p2 <= 3.0e38f && om > 0.0f)) {
         flag |= (p2 < 0.0f && om > 0.0f) ? FLAG_PSI_CLAMPED : FLAG_NONFINITE;
         p2 = 0.0f;
