@@ -53,6 +53,10 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr double kCs2 = 1.0 / 3.0;
 constexpr int kGraphChunk = 32;  // steps per captured graph (even: parity is preserved)
 constexpr uint32_t kStateMagic = 0x4c424d31u;  // "LBM1"
+// staging of the init and read-out kernels (lattices are staged a group at
+// a time): nodes per field and FP64 psi cells
+constexpr long long kStageNodes = 1LL << 24;
+constexpr long long kStageCells = 1LL << 25;
 // blob kind word: the precision, LBM_INPLACE for in-place storage, and
 // kBlobSwapped when an in-place state was saved in the swapped layout
 constexpr uint32_t kBlobSwapped = 0x10000u;
@@ -128,8 +132,13 @@ struct lbm_ctx {
     unsigned* d_status = nullptr;
     double* d_partials = nullptr;
     double* d_scalar = nullptr;
-    double* d_io = nullptr;      // staging: 4 * total_nodes doubles, indexed by node_off
-    double* d_psi = nullptr;     // read-out scratch: one FP64 psi plane per lattice
+    // staging of the init and read-out kernels, for a group of lattices at a
+    // time: d_io holds 4 fields of stage_nodes doubles, d_psi stage_cells
+    // FP64 psi cells (the read-out's plane); in-place storage also keeps the
+    // step's psi planes of every lattice in d_psi
+    double* d_io = nullptr;
+    double* d_psi = nullptr;
+    long long stage_nodes = 0, stage_cells = 0;
     // per-lattice invalid-input flags of the init kernel: page-locked host
     // memory that the kernel writes through its mapped address (m_bad); a
     // flag equal to bad_gen was set by the current init call
@@ -675,6 +684,29 @@ long long range_nodes(lbm_ctx* c, int lat0, int n_lat) {
     return last.node_off + (long long)last.nx * last.ny - c->lats[lat0].geom.node_off;
 }
 
+// First psi cell of lattice l in a plane that covers every lattice (the
+// kernels place lattice l's plane at f_off / 9), and one past its last.
+long long cell_lo(const lbm_ctx* c, int l) { return c->lats[l].geom.f_off / 9; }
+long long cell_hi(const lbm_ctx* c, int l) { return c->lats[l].geom.f_off / 9 + c->lats[l].geom.plane; }
+
+// End of the group of lattices starting at `l0` (at most `end`) whose nodes
+// and psi cells fit the staging buffers; every lattice fits on its own.
+int group_end(const lbm_ctx* c, int l0, int end) {
+    int l1 = l0 + 1;
+    while (l1 < end && range_nodes(const_cast<lbm_ctx*>(c), l0, l1 + 1 - l0) <= c->stage_nodes &&
+           cell_hi(c, l1) - cell_lo(c, l0) <= c->stage_cells)
+        ++l1;
+    return l1;
+}
+
+// A staging array holding the group that starts at node `nodes` (cells:
+// psi cell `cells`), shifted so that the kernels index it by geom.node_off
+// (geom.f_off / 9).
+template <typename P>
+P* cell_base(P* p, long long cells) {
+    return p ? (P*)((uintptr_t)p - (uintptr_t)(cells * (long long)sizeof(double))) : nullptr;
+}
+
 // Initial state of lattices [lat0, lat0 + n_lat) from host arrays that start
 // at lattice lat0's first node: one upload per field, one kernel launch.
 // Device address under which kernels reach a page-locked, mapped host
@@ -710,29 +742,34 @@ int init_range(lbm_ctx* c, int lat0, int n_lat, const double* rho, const double*
         if (rc) return rc;
         drop_graphs(c);
     }
-    const long long base = c->lats[lat0].geom.node_off;
-    const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
-    // staged through the device buffer d_io: a bulk copy, then the init
-    // kernel (faster than the kernel reading a mapped host buffer in place,
-    // whose scattered reads each pay the host link's latency)
-    double* d_rho = c->d_io + base;
-    double* d_ux = ux ? c->d_io + c->total_nodes + base : nullptr;
-    double* d_uy = uy ? c->d_io + 2 * c->total_nodes + base : nullptr;
-    CK(cudaMemcpyAsync(d_rho, rho, bytes, cudaMemcpyHostToDevice, c->stream));
-    if (ux) CK(cudaMemcpyAsync(d_ux, ux, bytes, cudaMemcpyHostToDevice, c->stream));
-    if (uy) CK(cudaMemcpyAsync(d_uy, uy, bytes, cudaMemcpyHostToDevice, c->stream));
-    const double* k_rho = c->d_io;
-    const double* k_ux = ux ? c->d_io + c->total_nodes : nullptr;
-    const double* k_uy = uy ? c->d_io + 2 * c->total_nodes : nullptr;
-    const LaunchSet ls = launch_set(c, lat0, n_lat);
+    // staged through the device buffer d_io, a group of lattices at a time:
+    // a bulk copy, then the init kernel (faster than the kernel reading a
+    // mapped host buffer in place, whose scattered reads each pay the host
+    // link's latency)
     if (++c->bad_gen == 0) c->bad_gen = 1;  // 0 is the value of a flag never set
-    cudaError_t e;
-    if (c->precision == LBM_FP64)
-        e = launch_init_f64(ls, k_rho, k_ux, k_uy, (double*)c->f[c->cur], c->m_bad, c->bad_gen, c->stream);
-    else
-        e = launch_init_f32(ls, k_rho, k_ux, k_uy, (float*)c->f[c->cur], c->m_bad, c->bad_gen, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
-    c->launches += 1;
+    const long long base = c->lats[lat0].geom.node_off;
+    const long long S = c->stage_nodes;
+    for (int a = lat0; a < lat0 + n_lat;) {
+        const int b = group_end(c, a, lat0 + n_lat);
+        const long long gb = c->lats[a].geom.node_off;
+        const size_t bytes = (size_t)range_nodes(c, a, b - a) * sizeof(double);
+        const long long o = gb - base;
+        CK(cudaMemcpyAsync(c->d_io, rho + o, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (ux) CK(cudaMemcpyAsync(c->d_io + S, ux + o, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (uy) CK(cudaMemcpyAsync(c->d_io + 2 * S, uy + o, bytes, cudaMemcpyHostToDevice, c->stream));
+        const double* k_rho = node_base(c->d_io, gb);
+        const double* k_ux = ux ? node_base(c->d_io + S, gb) : nullptr;
+        const double* k_uy = uy ? node_base(c->d_io + 2 * S, gb) : nullptr;
+        const LaunchSet ls = launch_set(c, a, b - a);
+        cudaError_t e;
+        if (c->precision == LBM_FP64)
+            e = launch_init_f64(ls, k_rho, k_ux, k_uy, (double*)c->f[c->cur], c->m_bad, c->bad_gen, c->stream);
+        else
+            e = launch_init_f32(ls, k_rho, k_ux, k_uy, (float*)c->f[c->cur], c->m_bad, c->bad_gen, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+        c->launches += 1;
+        a = b;
+    }
     // the host arrays may be pageable and the staging buffer is reused: wait,
     // then report invalid input found by the init kernel
     CK(cudaStreamSynchronize(c->stream));
@@ -783,35 +820,49 @@ int init_open(lbm_ctx* c, int lat, const double* rho, const double* ux, const do
 }
 
 // rho, v, p of lattices [lat0, lat0 + n_lat) into host arrays that start at
-// lattice lat0's first node: one kernel launch, one download per field.
+// lattice lat0's first node: per group of lattices that fits the staging
+// buffers, one or two kernel launches and one download per field (density
+// alone into a page-locked, mapped host buffer: one launch, no staging).
 int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, double* uy, double* p) {
-    const long long N = c->total_nodes;
-    double* d[4] = {c->d_io, c->d_io + N, c->d_io + 2 * N, c->d_io + 3 * N};
-    const LaunchSet ls = launch_set(c, lat0, n_lat);
-    cudaError_t e;
+    const long long S = c->stage_nodes;
     const long long base = c->lats[lat0].geom.node_off;
+    const bool density_only = !ux && !uy && !p;
     double* m_rho = (double*)mapped_device_ptr(rho);
-    if (!ux && !uy && !p) {  // density only: one light kernel, writing a mapped host buffer in place
-        double* out = m_rho ? node_base(m_rho, base) : d[0];
+    cudaError_t e;
+    if (density_only && m_rho) {
+        const LaunchSet ls = launch_set(c, lat0, n_lat);
+        double* out = node_base(m_rho, base);
         e = c->precision == LBM_FP64 ? launch_density_f64(ls, (const double*)c->f[c->cur], out, c->stream)
                                      : launch_density_f32(ls, (const float*)c->f[c->cur], out, c->stream);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
-        if (m_rho) {
-            CK(cudaStreamSynchronize(c->stream));
-            return LBM_OK;
-        }
-    } else {
-        e = c->precision == LBM_FP64
-                ? launch_moments_f64(ls, (const double*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream)
-                : launch_moments_f32(ls, (const float*)c->f[c->cur], c->d_psi, d[0], d[1], d[2], d[3], c->stream);
-        c->launches += 2;
+        CK(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
-    const size_t bytes = (size_t)range_nodes(c, lat0, n_lat) * sizeof(double);
     double* h[4] = {rho, ux, uy, p};
-    for (int k = 0; k < 4; ++k)
-        if (h[k]) CK(cudaMemcpyAsync(h[k], d[k] + base, bytes, cudaMemcpyDeviceToHost, c->stream));
+    for (int a = lat0; a < lat0 + n_lat;) {
+        const int b = group_end(c, a, lat0 + n_lat);
+        const long long gb = c->lats[a].geom.node_off;
+        const LaunchSet ls = launch_set(c, a, b - a);
+        double* d[4];
+        for (int k = 0; k < 4; ++k) d[k] = node_base(c->d_io + k * S, gb);
+        if (density_only) {
+            e = c->precision == LBM_FP64 ? launch_density_f64(ls, (const double*)c->f[c->cur], d[0], c->stream)
+                                         : launch_density_f32(ls, (const float*)c->f[c->cur], d[0], c->stream);
+            c->launches += 1;
+        } else {
+            double* psi = cell_base(c->d_psi, cell_lo(c, a));
+            e = c->precision == LBM_FP64
+                    ? launch_moments_f64(ls, (const double*)c->f[c->cur], psi, d[0], d[1], d[2], d[3], c->stream)
+                    : launch_moments_f32(ls, (const float*)c->f[c->cur], psi, d[0], d[1], d[2], d[3], c->stream);
+            c->launches += 2;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
+        const size_t bytes = (size_t)range_nodes(c, a, b - a) * sizeof(double);
+        for (int k = 0; k < 4; ++k)
+            if (h[k]) CK(cudaMemcpyAsync(h[k] + (gb - base), c->d_io + k * S, bytes, cudaMemcpyDeviceToHost, c->stream));
+        a = b;
+    }
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -904,8 +955,24 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     // reduction scratch: 4 partial sums per block and lattice, 3 totals per lattice
     if (!rc) rc = dev_alloc(c, &c->d_partials, 4 * (size_t)kMassBlocks * n * sizeof(double));
     if (!rc) rc = dev_alloc(c, &c->d_scalar, 3 * (size_t)n * sizeof(double));
-    if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->total_nodes * sizeof(double));
-    if (!rc) rc = dev_alloc(c, &c->d_psi, ((size_t)c->total_elems / 9 + 64) * sizeof(double));
+    // staging for a group of lattices at a time: at least the largest
+    // lattice, at most kStageNodes nodes (and kStageCells psi cells) unless
+    // one lattice needs more
+    long long max_plane = 0;
+    for (const auto& L : c->lats) max_plane = std::max(max_plane, L.geom.plane);
+    const long long total_cells = c->total_elems / 9 + 64;
+    // LBM_STAGE_NODES / LBM_STAGE_CELLS (read here) lower the two limits, so
+    // that a test can make small batches take several groups
+    long long lim_nodes = kStageNodes, lim_cells = kStageCells;
+    if (const char* v = getenv("LBM_STAGE_NODES")) lim_nodes = std::max(1LL, std::min(kStageNodes, atoll(v)));
+    if (const char* v = getenv("LBM_STAGE_CELLS")) lim_cells = std::max(1LL, std::min(kStageCells, atoll(v)));
+    c->stage_nodes = std::max(c->max_nodes, std::min(c->total_nodes, lim_nodes));
+    c->stage_cells = std::max(max_plane, std::min(total_cells, lim_cells));
+    if (!rc) rc = dev_alloc(c, &c->d_io, 4 * (size_t)c->stage_nodes * sizeof(double));
+    // in place, the step also keeps one psi plane of every lattice here
+    const size_t psi_bytes = std::max((size_t)c->stage_cells * sizeof(double),
+                                      c->inplace ? (size_t)total_cells * c->elem : (size_t)0);
+    if (!rc) rc = dev_alloc(c, &c->d_psi, psi_bytes);
     if (!rc && cudaHostAlloc((void**)&c->h_bad, n * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         c->h_bad = nullptr;
@@ -1091,17 +1158,25 @@ namespace {
 // Mass and momentum of lattices [lat0, lat0 + n_lat) into out[3k .. 3k + 2];
 // the status bits of every lattice come back in st.
 int totals_range(lbm_ctx* c, int lat0, int n_lat, double* out, std::vector<unsigned>& st) {
-    const long long N = c->total_nodes;
-    const LaunchSet ls = launch_set(c, lat0, n_lat);
-    cudaError_t e;
-    if (c->precision == LBM_FP64)
-        e = launch_totals_f64(ls, (const double*)c->f[c->cur], c->d_psi, c->d_io, c->d_io + N, c->d_io + 2 * N,
-                              c->d_partials, c->d_scalar, c->stream);
-    else
-        e = launch_totals_f32(ls, (const float*)c->f[c->cur], c->d_psi, c->d_io, c->d_io + N, c->d_io + 2 * N,
-                              c->d_partials, c->d_scalar, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "totals kernels");
-    c->launches += 3;
+    const long long S = c->stage_nodes;
+    for (int a = lat0; a < lat0 + n_lat;) {
+        const int b = group_end(c, a, lat0 + n_lat);
+        const long long gb = c->lats[a].geom.node_off;
+        const LaunchSet ls = launch_set(c, a, b - a);
+        double* psi = cell_base(c->d_psi, cell_lo(c, a));
+        double* d[3];
+        for (int k = 0; k < 3; ++k) d[k] = node_base(c->d_io + k * S, gb);
+        cudaError_t e;
+        if (c->precision == LBM_FP64)
+            e = launch_totals_f64(ls, (const double*)c->f[c->cur], psi, d[0], d[1], d[2], c->d_partials,
+                                  c->d_scalar + 3 * (a - lat0), c->stream);
+        else
+            e = launch_totals_f32(ls, (const float*)c->f[c->cur], psi, d[0], d[1], d[2], c->d_partials,
+                                  c->d_scalar + 3 * (a - lat0), c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "totals kernels");
+        c->launches += 3;
+        a = b;
+    }
     CK(cudaMemcpyAsync(out, c->d_scalar, 3 * (size_t)n_lat * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return read_status(c, st);
 }

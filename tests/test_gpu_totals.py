@@ -138,3 +138,54 @@ def test_momentum_rejects_bad_arguments():
         lbm._check(lbm.load().lbm_totals_all(b.ctx, None))
     assert e.value.code == lbm.LBM_EINVAL
     b.close()
+
+
+def test_staging_in_groups_changes_nothing(monkeypatch):
+    """Init and read-outs stage a group of lattices at a time when the batch
+    exceeds the staging buffers; with tiny buffers (every lattice a group of
+    its own, or a few together) the results equal one-group staging bit for
+    bit, also with velocities and for in-place storage."""
+    specs = [small_spec(70, 45, walls=True, seed=71), small_spec(130, 9, seed=72), stratified_channel(True),
+             small_spec(33, 300, seed=73, shape="bubble"), small_spec(5, 3, seed=74)]
+    ux = [np.full_like(s.rho, 0.01) for s in specs]
+    uy = [np.full_like(s.rho, -0.02) for s in specs]
+
+    def run(precision):
+        b = lbm.Batch(specs, precision)
+        for i, s in enumerate(specs):
+            lbm.lbm_init_fields(b.ctx, i, s.rho, ux[i], uy[i])
+        rho_all = np.ascontiguousarray(np.concatenate([s.rho.ravel() for s in specs]))
+        b.step(3)
+        lbm.lbm_init_fields(b.ctx, 3, specs[3].rho)                    # one lattice again
+        b.step(4)
+        n = sum(s.nodes for s in specs)
+        out = [np.empty(n) for _ in range(4)]
+        lbm.lbm_read_moments_all(b.ctx, *out, allow_flags=True)
+        dens = np.empty(n)
+        lbm.lbm_read_moments_all(b.ctx, dens, allow_flags=True)       # density alone
+        tot = b.totals(allow_flags=True)
+        per = [b.moments(i, allow_flags=True) for i in range(len(specs))]
+        b2 = lbm.Batch(specs, precision)
+        lbm.lbm_init_fields_all(b2.ctx, rho_all)
+        b2.step(2)
+        out2 = np.empty(n)
+        lbm.lbm_read_moments_all(b2.ctx, out2, allow_flags=True)
+        b.close()
+        b2.close()
+        return out, dens, tot, per, out2
+
+    for precision in ("fp32_dev", "fp64", "fp32_dev_inplace"):
+        ref = run(precision)
+        for nodes, cells in (("1", "1"), ("20000", "40000")):
+            monkeypatch.setenv("LBM_STAGE_NODES", nodes)
+            monkeypatch.setenv("LBM_STAGE_CELLS", cells)
+            got = run(precision)
+            monkeypatch.delenv("LBM_STAGE_NODES")
+            monkeypatch.delenv("LBM_STAGE_CELLS")
+            for a, b in zip(got[0], ref[0]):
+                assert np.array_equal(a, b), precision
+            assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+            for pa, pb in zip(got[3], ref[3]):
+                for a, b in zip(pa, pb):
+                    assert np.array_equal(a, b)
+            assert np.array_equal(got[4], ref[4])
