@@ -210,12 +210,11 @@ def vapour_radius(rho: np.ndarray, rho_l: float, rho_g: float) -> float:
     return float(np.sqrt(np.count_nonzero(rho < 0.5 * (rho_l + rho_g)) / np.pi))
 
 
-def nucleus_run(radii: Sequence[float], rho_liquid: float, steps: int, every: int = 1000, n: int = 401,
-                t_over_tc: float = 0.5, a: float = 0.5, tau_nu: float = 0.6, eps: float = 1.86, width: float = 5.0,
-                stream=None) -> List[dict]:
-    """Critical nucleus (Sec. 3.2, Eq. 18, Fig. 5): vapour bubbles of the given
-    radii at the coexistence vapour density, centred in liquid of density
-    rho_liquid on n x n periodic lattices; radius histories r(t)."""
+def nucleus_specs(radii: Sequence[float], rho_liquid: float, n: int = 401, t_over_tc: float = 0.5, a: float = 0.5,
+                  tau_nu: float = 0.6, eps: float = 1.86, width: float = 5.0) -> List[inputs.LatticeSpec]:
+    """The lattices of nucleus_run: one n x n periodic lattice per radius, a
+    vapour bubble at the coexistence vapour density centred in liquid of
+    density rho_liquid."""
     c = inputs.coexistence(t_over_tc)
     T = t_over_tc * inputs.critical_temperature() * a
     specs = []
@@ -223,6 +222,17 @@ def nucleus_run(radii: Sequence[float], rho_liquid: float, steps: int, every: in
         rho = inputs.tanh_profile(n, n, (n - 1) / 2, (n - 1) / 2, R, rho_liquid, c["rho_g"], width)
         specs.append(inputs.LatticeSpec(n, n, T, inputs.relax_rates(tau_nu), eps, rho, rho_ref=c["rho_g"],
                                         a=a, b=4.0, meta={"R0": R}))
+    return specs
+
+
+def nucleus_run(radii: Sequence[float], rho_liquid: float, steps: int, every: int = 1000, n: int = 401,
+                t_over_tc: float = 0.5, a: float = 0.5, tau_nu: float = 0.6, eps: float = 1.86, width: float = 5.0,
+                stream=None) -> List[dict]:
+    """Critical nucleus (Sec. 3.2, Eq. 18, Fig. 5): vapour bubbles of the given
+    radii at the coexistence vapour density, centred in liquid of density
+    rho_liquid on n x n periodic lattices; radius histories r(t)."""
+    c = inputs.coexistence(t_over_tc)
+    specs = nucleus_specs(radii, rho_liquid, n, t_over_tc, a, tau_nu, eps, width)
     b = lbm.Batch(specs, "fp32_dev", stream=stream)
     b.init()
     hist = [{"R0": R, "t": [], "r": [], "rho_centre": [], "rho_liquid": []} for R in radii]
