@@ -371,12 +371,10 @@ def main():
     # ---- FP32 deviation storage (the product path)
     b32 = lbm.Batch(specs, "fp32_dev", stream=stream)
     b32.init()
-    # tile shape: the fastest of the plain and pipelined shapes on flushed
-    # single steps (after a warm-up, so the first shape measured pays no
-    # first-launch cost); the TMA-staged shapes run at about half the speed
-    # and are not tried
+    # tile shape: the fastest of every shape on flushed single steps (after a
+    # warm-up, so the first shape measured pays no first-launch cost)
     timed_steps(torch, b32.ctx, lbm, stream, flush, 30)
-    sweep = [t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) != lbm.LBM_TILE_TMA]
+    sweep = list(range(lbm.lbm_tile_count()))
     plain = [t for t in sweep if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_PLAIN]
     tile_ms = {}
     for t in sweep:
@@ -415,7 +413,9 @@ def main():
     for name in SUSTAINED:
         lspecs = inputs.WORKLOADS[name]()
         lnodes = sum(s.nodes for s in lspecs)
-        lms, lt, trial = sustained_steps(torch, lbm, lspecs, stream, plain)
+        # every shape, the TMA-staged ones too where the batch allows them
+        tiles = sweep if len(lspecs) <= 64 else [t for t in sweep if lbm.lbm_tile_kind(t) != lbm.LBM_TILE_TMA]
+        lms, lt, trial = sustained_steps(torch, lbm, lspecs, stream, tiles)
         gbs = ALG_BYTES_FP32 * lnodes / (lms * 1e-3) / 1e9
         entry = {"nodes": lnodes, "working_set_bytes": 2 * 36 * lnodes, "tile": lbm.lbm_tile_shape(lt),
                  "tile_index": lt, "steps": 256, "ms_per_step": lms, "MLUPS": lnodes / (lms * 1e-3) / 1e6,

@@ -7,7 +7,7 @@
 // it needs, per population a, the post-collision values of the tile plus a
 // two-cell frame: one 3-D TMA box load per population ({TX+8, TY+4, 1} at
 // stored (x0 + kGX - 4, y0 + kGY - 2, a); the x origin is 16-byte aligned) and,
-// for lattices with walls, one 2-D box of the wall mask. The kernel takes the
+// for a tile within two cells of a solid cell, one 2-D box of the wall mask. The kernel takes the
 // tiles at least two cells away from every lattice edge, so a box holds the
 // nodes it stands for and no pull wraps; the plain kernel does the others.
 // Loads for the next S - 1 tiles are in flight (an mbarrier per stage) while
@@ -115,8 +115,8 @@ struct TmaBox {
     static_assert(BOX_BYTES % 128 == 0, "population boxes must stay 128-byte aligned");
 };
 
-template <int TX, int TY, int RY, int S>
-__global__ void __launch_bounds__(TX*(TY / RY), 1)
+template <int TX, int TY, int RY, int S, int MINB>
+__global__ void __launch_bounds__(TX*(TY / RY), MINB)
     step_tma_kernel(const TmaArgs A, const __grid_constant__ TmaMaps M, const __grid_constant__ PhysTable<float> PT) {
     using B = TmaBox<TX, TY>;
     constexpr int TYT = TY / RY;
@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
     // thread 0: arm stage s for tile t and issue its box loads
     auto issue = [&](int t, int s) {
         const Tile tl = A.tiles[t];
-        const bool has_mask = geom_mask(A.geom[tl.lat]);
+        // a tile with no solid cell within two cells needs no mask box
+        const bool has_mask = geom_mask(A.geom[tl.lat]) && !tl.clear;
         unsigned char* st = smem + s * B::STAGE_BYTES;
         mbar_arrive_expect_tx(&bars[s], 9 * B::BOX_BYTES + (has_mask ? B::MASK_BYTES : 0) + A.extra_tx);
         const CUtensorMap* fm = &M.f[tl.lat];
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
         const Phys<float>& P = *Pp;
         const float* __restrict__ st = reinterpret_cast<const float*>(smem + s * B::STAGE_BYTES);
         const uint8_t* __restrict__ ms =
-            geom_mask(g) ? reinterpret_cast<const uint8_t*>(smem + s * B::STAGE_BYTES + 9 * B::BOX_BYTES) : nullptr;
+            geom_mask(g) && !tl.clear ? reinterpret_cast<const uint8_t*>(smem + s * B::STAGE_BYTES + 9 * B::BOX_BYTES)
+                                      : nullptr;
         const float rho_ref = P.rho_ref;
         unsigned flag = 0;
 
@@ -250,7 +252,9 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
         if (x < g.nx)
             f32_collide_store<RY, SW>(f, live, drho, rho, psi, s_psi, lx, threadIdx.y * RY, ms != nullptr, P,
                                       A.fout + g.f_off, g, x, tl.y0 + threadIdx.y * RY);
-        __syncthreads();  // psi tile is rewritten by the next tile
+        // the psi tile is rewritten by the next tile only after the barrier
+        // at the top of the loop (__syncthreads_or), which every thread
+        // reaches after this collision
     }
 
     if (failed && tid == 0) {
@@ -269,34 +273,36 @@ __global__ void __launch_bounds__(TX*(TY / RY), 1)
 // ---------------------------------------------------------------- host side
 
 template <int TX, int TY, int RY, int S>
+constexpr size_t tma_smem_bytes() {
+    using B = TmaBox<TX, TY>;
+    return (size_t)S * B::STAGE_BYTES + (((TX + 2) * (TY + 2) * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
+}
+
+template <int TX, int TY, int RY, int S, int MINB>
 static cudaError_t launch_tma_tile(int grid, const TmaArgs& a, const TmaMaps& maps, const PhysTable<float>& table,
                                    cudaStream_t s) {
-    using B = TmaBox<TX, TY>;
-    constexpr int SW = TX + 2, SH = TY + 2;
-    const size_t smem = (size_t)S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
+    const size_t smem = tma_smem_bytes<TX, TY, RY, S>();
     static bool configured = false;  // per process; attributes are per device but identical
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<TX, TY, RY, S>,
+        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<TX, TY, RY, S, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    step_tma_kernel<TX, TY, RY, S><<<grid, dim3(TX, TY / RY), smem, s>>>(a, maps, table);
+    step_tma_kernel<TX, TY, RY, S, MINB><<<grid, dim3(TX, TY / RY), smem, s>>>(a, maps, table);
     return cudaGetLastError();
 }
 
-template <int TX, int TY, int RY, int S>
+template <int TX, int TY, int RY, int S, int MINB>
 static int tma_occupancy() {
-    using B = TmaBox<TX, TY>;
-    constexpr int SW = TX + 2, SH = TY + 2;
-    const size_t smem = (size_t)S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
-    if (cudaFuncSetAttribute(step_tma_kernel<TX, TY, RY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = tma_smem_bytes<TX, TY, RY, S>();
+    if (cudaFuncSetAttribute(step_tma_kernel<TX, TY, RY, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma_kernel<TX, TY, RY, S>, TX * (TY / RY), smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma_kernel<TX, TY, RY, S, MINB>, TX * (TY / RY), smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -304,13 +310,14 @@ static int tma_occupancy() {
     return n;
 }
 
-// TMA variants: {TX, TY, RY, stages}
-#define LBM_TMA_VARIANTS(X) X(0, 32, 8, 1, 3) X(1, 32, 16, 2, 2) X(2, 64, 8, 1, 2) X(3, 32, 8, 1, 4)
+// TMA variants: {TX, TY, RY, stages, minimum resident CTAs per SM (the
+// register cap)}
+#define LBM_TMA_VARIANTS(X) X(0, 32, 8, 1, 3, 3) X(1, 32, 16, 2, 2, 3) X(2, 32, 16, 2, 2, 4) X(3, 32, 16, 2, 3, 2)
 
 int tma_variant_count() { return 4; }
 
 void tma_variant_shape(int v, int* tx, int* ty) {
-#define LBM_SHAPE(i, a, b, r, s) \
+#define LBM_SHAPE(i, a, b, r, s, m) \
     if (v == i) {                \
         *tx = a;                 \
         *ty = b;                 \
@@ -328,8 +335,8 @@ int tma_plain_partner(int v) {
 }
 
 int tma_blocks_per_sm(int v) {
-#define LBM_OCC(i, a, b, r, s) \
-    if (v == i) return tma_occupancy<a, b, r, s>();
+#define LBM_OCC(i, a, b, r, s, m) \
+    if (v == i) return tma_occupancy<a, b, r, s, m>();
     LBM_TMA_VARIANTS(LBM_OCC)
 #undef LBM_OCC
     return 0;
@@ -338,8 +345,8 @@ int tma_blocks_per_sm(int v) {
 cudaError_t launch_step_tma(int v, int grid, const TmaArgs& args, const TmaMaps& maps,
                             const PhysTable<float>& table, cudaStream_t s) {
     if (args.n_tiles <= 0) return cudaSuccess;
-#define LBM_LAUNCH(i, a, b, r, st) \
-    if (v == i) return launch_tma_tile<a, b, r, st>(grid, args, maps, table, s);
+#define LBM_LAUNCH(i, a, b, r, st, m) \
+    if (v == i) return launch_tma_tile<a, b, r, st, m>(grid, args, maps, table, s);
     LBM_TMA_VARIANTS(LBM_LAUNCH)
 #undef LBM_LAUNCH
     return cudaErrorInvalidValue;
