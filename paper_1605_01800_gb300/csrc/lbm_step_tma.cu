@@ -125,9 +125,13 @@ __global__ void __launch_bounds__(TX*(TY / RY), MINB)
     constexpr int SH = TY + 2;
     constexpr int NH = 2 * SW + 2 * TY;
     constexpr int NHT = (NH + NT - 1) / NT;
+    constexpr int PSI_BYTES = ((SH * SW * 4 + 15) / 16) * 16;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float* s_psi = reinterpret_cast<float*>(smem + S * B::STAGE_BYTES);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * B::STAGE_BYTES + ((SH * SW * 4 + 15) / 16) * 16);
+    // two psi tiles for alternate tiles: a thread may fill the next tile's
+    // while others still read this one's, so one barrier per tile suffices
+    float* const s_psi2[2] = {reinterpret_cast<float*>(smem + S * B::STAGE_BYTES),
+                              reinterpret_cast<float*>(smem + S * B::STAGE_BYTES + PSI_BYTES)};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * B::STAGE_BYTES + 2 * PSI_BYTES);
 
     const int tid = threadIdx.y * TX + threadIdx.x;
     if (tid == 0) {
@@ -161,13 +165,13 @@ __global__ void __launch_bounds__(TX*(TY / RY), MINB)
     for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x, ++k) {
         const int s = k % S;
         const uint32_t parity = (uint32_t)((k / S) & 1);
+        // each thread waits for the stage itself; whether every wait
+        // succeeded is agreed at the tile's one barrier below (a thread whose
+        // wait gave up reads a partial stage there, harmlessly, and stores
+        // nothing)
         const bool ok = mbar_wait_bounded(&bars[s], parity, A.wait_limit);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            if (tid == 0) atomicOr(&A.status[A.tiles[t].lat], FLAG_TIMEOUT);
-            break;
-        }
         const Tile tl = A.tiles[t];
+        float* const s_psi = s_psi2[k & 1];
         const Geom g = A.geom[tl.lat];
         const Phys<float>* __restrict__ Pp = &PT.p[tl.lat];
         const Phys<float>& P = *Pp;
@@ -238,7 +242,12 @@ __global__ void __launch_bounds__(TX*(TY / RY), MINB)
                 s_psi[cy * SW + cx] = ph;
             }
         }
-        __syncthreads();  // stage s consumed, psi tile complete
+        // stage s consumed, psi tile complete; and every wait succeeded
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            if (tid == 0) atomicOr(&A.status[tl.lat], FLAG_TIMEOUT);
+            break;
+        }
 
         if (tid == 0) {
             const int tn = t + S * gridDim.x;
@@ -252,9 +261,8 @@ __global__ void __launch_bounds__(TX*(TY / RY), MINB)
         if (x < g.nx)
             f32_collide_store<RY, SW>(f, live, drho, rho, psi, s_psi, lx, threadIdx.y * RY, ms != nullptr, P,
                                       A.fout + g.f_off, g, x, tl.y0 + threadIdx.y * RY);
-        // the psi tile is rewritten by the next tile only after the barrier
-        // at the top of the loop (__syncthreads_or), which every thread
-        // reaches after this collision
+        // this psi tile is written again two tiles on, after the next
+        // tile's barrier, which every thread reaches after this collision
     }
 
     if (failed && tid == 0) {
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(TX*(TY / RY), MINB)
 template <int TX, int TY, int RY, int S>
 constexpr size_t tma_smem_bytes() {
     using B = TmaBox<TX, TY>;
-    return (size_t)S * B::STAGE_BYTES + (((TX + 2) * (TY + 2) * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
+    return (size_t)S * B::STAGE_BYTES + 2 * (((TX + 2) * (TY + 2) * 4 + 15) / 16) * 16 + S * sizeof(uint64_t);
 }
 
 template <int TX, int TY, int RY, int S, int MINB>
