@@ -212,6 +212,19 @@ int lbm_init_fields_all(lbm_ctx* ctx, const double* rho, const double* ux, const
  * stream, whole chunks of `graph_chunk` steps replay a captured CUDA graph. */
 int lbm_step(lbm_ctx* ctx, int n);
 
+/* One time step in two launches (asynchronous on the context's stream), for
+ * overlapping an x-slab's halo exchange with the step:
+ *   LBM_STEP_EDGE      the tiles within two cells of an open x edge (those
+ *                      whose nodes the halo holds; none without x-slabs);
+ *   LBM_STEP_INTERIOR  every other tile.
+ * The step is complete (the state advances, the step count grows) once both
+ * parts are launched, in either order; the result is bitwise lbm_step(ctx, 1).
+ * LBM_EINVAL for another part value, a part launched twice for one step, and
+ * lbm_step while a split step is half done. */
+#define LBM_STEP_EDGE 1
+#define LBM_STEP_INTERIOR 2
+int lbm_step_part(lbm_ctx* ctx, int part);
+
 /* Macroscopic fields of lattice `lat` at the current time: rho = sum_a f_a,
  * v of Eq. 6 (with the force of Eq. 7), p of Eq. 10. Host outputs of nx*ny
  * doubles; any may be NULL (with ux, uy and p all NULL only the density is
@@ -330,21 +343,28 @@ int lbm_get_state_view(lbm_ctx* ctx, int lat, lbm_state_view* view);
 #define LBM_HALO_ROWS 12
 int lbm_set_open_x(lbm_ctx* ctx, int lat, const uint8_t* halo_mask);
 
-/* Halo exchange of a slab (asynchronous on the context's stream; device
- * buffers of LBM_HALO_ROWS*ny elements of the storage type: 4-byte floats
- * for the FP32 precisions, 8-byte doubles for LBM_FP64; rows k*ny .. k*ny +
- * ny - 1 hold value k of every row y).
+/* Halo exchange of a slab (asynchronous on `cuda_stream`, NULL: the
+ * context's stream; device buffers of LBM_HALO_ROWS*ny elements of the
+ * storage type: 4-byte floats for the FP32 precisions, 8-byte doubles for
+ * LBM_FP64; rows k*ny .. k*ny + ny - 1 hold value k of every row y).
  *   lbm_halo_pack    writes into dev_out what the neighbour on `side`
  *                    (0: left, x < 0; 1: right, x >= nx) pulls from this
  *                    slab's current state.
  *   lbm_halo_unpack  writes the halo packed by the neighbour on `side` (its
  *                    pack of the opposite side) into this slab's frame.
  * The transport between the two (NCCL send/recv, a peer copy, a host copy)
- * is the caller's; order it with the context's stream. Per step: step, pack
- * both sides, exchange, unpack both sides. LBM_EINVAL for a lattice not
- * open in x, a side other than 0 or 1, or a null buffer. */
-int lbm_halo_pack(lbm_ctx* ctx, int lat, int side, void* dev_out);
-int lbm_halo_unpack(lbm_ctx* ctx, int lat, int side, const void* dev_in);
+ * is the caller's, and so is the ordering of a stream other than the
+ * context's with it. Per step: step, pack both sides, exchange, unpack both
+ * sides. To overlap the exchange with the step, split the step with
+ * lbm_step_part: launch LBM_STEP_EDGE, pack (on another stream, ordered after
+ * it), exchange and unpack there while LBM_STEP_INTERIOR runs, and order the
+ * next step after the unpack. During a split step the calls address the
+ * buffer the step writes: a pack needs the edge part launched first; an
+ * unpack writes the frame the next step reads (no part writes it).
+ * LBM_EINVAL for a lattice not open in x, a side other than 0 or 1, a null
+ * buffer, or a pack before a split step's edge part. */
+int lbm_halo_pack(lbm_ctx* ctx, int lat, int side, void* dev_out, void* cuda_stream);
+int lbm_halo_unpack(lbm_ctx* ctx, int lat, int side, const void* dev_in, void* cuda_stream);
 
 /* Largest ny accepted by lbm_total_mass_fp32_noalloc. */
 #define LBM_NOALLOC_MAX_NY 32768

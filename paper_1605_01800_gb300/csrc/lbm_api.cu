@@ -101,6 +101,8 @@ struct lbm_ctx {
     Phys<double>* d_phys_d = nullptr;
     Tile* d_tiles = nullptr;
     int n_tiles = 0;             // tiles of the plain kernel
+    int n_edge = 0;              // the first n_edge of them: within two cells of an open x edge
+    int part_done = 0;           // parts of a split step (lbm_step_part) launched so far
     // pipelined variants: the full wall-free tiles go to the persistent kernel
     // (d_fast, n_fast, pipe_grid CTAs), the rest (d_tiles) to the plain kernel
     // of the same node tile; TMA variants take the tiles two cells or more
@@ -430,6 +432,15 @@ int build_tiles(lbm_ctx* c, int tile_index) {
         const bool fast = t.clear && full && g.nx >= 4 && g.ny >= 4 && c->lats[t.lat].desc.eos.kind == LBM_EOS_CS;
         return !fast;
     });
+    // the tiles within two cells of an open x edge (an x-slab's cuts) go
+    // first of all: a split step (lbm_step_part) launches them apart, so
+    // that the halo they feed can be exchanged while the rest runs
+    auto open_edge = [&](const Tile& t) {
+        const Geom& g = c->lats[t.lat].geom;
+        return geom_open_x(g) && (t.x0 < 2 || t.x0 + tx > g.nx - 2);
+    };
+    std::stable_partition(tiles.begin(), tiles.end(), open_edge);
+    const int n_edge = (int)std::count_if(tiles.begin(), tiles.end(), open_edge);
     std::vector<TileGeom> tgeo(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) tgeo[k] = TileGeom{c->lats[tiles[k].lat].geom, tiles[k]};
     Tile* d = nullptr;
@@ -497,6 +508,7 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     c->d_tiles = d;
     c->d_tgeo = dg;
     c->n_tiles = (int)tiles.size();
+    c->n_edge = n_edge;
     c->d_fast = df;
     c->n_fast = (int)fast.size();
     c->pipe_grid = pipe ? (int)std::min<long long>(c->n_fast, (long long)per_sm * sms) : 0;
@@ -565,9 +577,17 @@ LaunchSet launch_set(lbm_ctx* c, int lat0, int n_lat) {
     return LaunchSet{c->d_geom, c->d_phys_d, c->d_mask, lat0, n_lat, mx, me, state_layout(c)};
 }
 
-cudaError_t launch_one_step(lbm_ctx* c, int src) {
-    cudaError_t e;
+// Parts of a time step: every tile, the tiles within two cells of an open
+// x edge (the first n_edge of the plain list), or all the others.
+constexpr int kPartAll = 3;
+constexpr int kPartEdge = LBM_STEP_EDGE;
+constexpr int kPartInterior = LBM_STEP_INTERIOR;
+
+// One step launch (or one part of it) from buffer `src` into buffer 1 - src.
+cudaError_t launch_one_step(lbm_ctx* c, int src, int part = kPartAll) {
+    cudaError_t e = cudaSuccess;
     if (c->inplace) {
+        if (!(part & kPartInterior)) return cudaSuccess;  // in place holds no open lattice: no edge part
         int tx = 0, ty = 0;
         tile_shape(c->tile_index, &tx, &ty);
         const int layout = src == 0 ? kLayoutNatural : kLayoutSwapped;
@@ -579,35 +599,37 @@ cudaError_t launch_one_step(lbm_ctx* c, int src) {
                                         (float*)c->d_psi, c->d_status, layout, c->stream);
         return e;
     }
+    // the plain kernel's share of this part: [first, first + count) of its list
+    const int first = part == kPartInterior ? c->n_edge : 0;
+    const int count = part == kPartEdge ? c->n_edge : (part == kPartInterior ? c->n_tiles - c->n_edge : c->n_tiles);
+    const bool open = any_open_x(c);
     if (c->precision == LBM_FP64) {
-        StepArgs<double> a{c->d_tiles, c->d_geom, c->d_phys_d, (const double*)c->f[src],
-                           (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-        e = launch_step_f64(c->tile_index, c->n_tiles, a, c->stream, any_open_x(c));
-    } else if (is_pipe(c->tile_index)) {
+        StepArgs<double> a{c->d_tiles + first, c->d_geom, c->d_phys_d, (const double*)c->f[src],
+                           (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo + first};
+        return launch_step_f64(c->tile_index, count, a, c->stream, open);
+    }
+    StepArgs<float> a{c->d_tiles + first, c->d_geom, c->d_phys_f, (const float*)c->f[src], (float*)c->f[1 - src],
+                      c->d_mask, c->d_status, c->d_tgeo + first};
+    int plain_shape = c->tile_index;
+    if (is_pipe(c->tile_index)) {
         const int v = c->tile_index - pipe_first();
-        const PhysTable<float>* table = c->n <= kParamLattices ? c->h_table : nullptr;
-        PipeArgs pa{c->d_fast, c->n_fast, c->d_phys_f, (const float*)c->f[src], (float*)c->f[1 - src], c->d_status};
-        e = launch_step_pipe(v, c->pipe_grid, pa, table, c->stream);
-        if (e == cudaSuccess && c->n_tiles > 0) {
-            StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
-                              (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-            e = launch_step_f32(pipe_plain_partner(v), c->n_tiles, a, c->h_table, c->stream, any_open_x(c));
+        plain_shape = pipe_plain_partner(v);
+        if (part & kPartInterior) {  // the persistent kernel's tiles are all interior
+            const PhysTable<float>* table = c->n <= kParamLattices ? c->h_table : nullptr;
+            PipeArgs pa{c->d_fast, c->n_fast, c->d_phys_f, (const float*)c->f[src], (float*)c->f[1 - src],
+                        c->d_status};
+            e = launch_step_pipe(v, c->pipe_grid, pa, table, c->stream);
         }
     } else if (c->tile_index >= kTileCount) {
         const int v = c->tile_index - kTileCount;
-        TmaArgs ta{c->d_tma, c->n_tma, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status,
-                   c->tma_wait_limit, c->tma_extra_tx};
-        e = launch_step_tma(v, c->tma_grid[v], ta, *c->h_maps[v][src], *c->h_table, c->stream);
-        if (e == cudaSuccess && c->n_tiles > 0) {
-            StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
-                              (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-            e = launch_step_f32(tma_plain_partner(v), c->n_tiles, a, c->h_table, c->stream, any_open_x(c));
+        plain_shape = tma_plain_partner(v);
+        if (part & kPartInterior) {  // as are the TMA kernel's
+            TmaArgs ta{c->d_tma, c->n_tma, c->d_geom, c->d_phys_f, (float*)c->f[1 - src], c->d_status,
+                       c->tma_wait_limit, c->tma_extra_tx};
+            e = launch_step_tma(v, c->tma_grid[v], ta, *c->h_maps[v][src], *c->h_table, c->stream);
         }
-    } else {
-        StepArgs<float> a{c->d_tiles, c->d_geom, c->d_phys_f, (const float*)c->f[src],
-                          (float*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo};
-        e = launch_step_f32(c->tile_index, c->n_tiles, a, c->h_table, c->stream, any_open_x(c));
     }
+    if (e == cudaSuccess && count > 0) e = launch_step_f32(plain_shape, count, a, c->h_table, c->stream, open);
     return e;
 }
 
@@ -1082,6 +1104,8 @@ int lbm_step(lbm_ctx* c, int n) {
     if (n > 1 && any_open_x(c))
         return fail(LBM_EINVAL, "n=%d: a lattice open in x needs its halo exchanged between steps; step one "
                                 "at a time", n);
+    if (n > 0 && c->part_done)
+        return fail(LBM_EINVAL, "a split step (lbm_step_part) is half done: launch its other part first");
     int done = 0;
     if (capturable_stream(c->stream)) {
         while (n - done >= kGraphChunk) {
@@ -1097,6 +1121,24 @@ int lbm_step(lbm_ctx* c, int n) {
         cudaError_t e = launch_one_step(c, c->cur);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         c->launches += launches_per_step(c);
+        c->cur ^= 1;
+        c->steps += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_step_part(lbm_ctx* c, int part) {
+    Range range("lbm_step_part");
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (part != LBM_STEP_EDGE && part != LBM_STEP_INTERIOR)
+        return fail(LBM_EINVAL, "part=%d must be LBM_STEP_EDGE or LBM_STEP_INTERIOR", part);
+    if (c->part_done & part) return fail(LBM_EINVAL, "part %d of this step was launched already", part);
+    cudaError_t e = launch_one_step(c, c->cur, part);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    c->launches += part == LBM_STEP_EDGE ? (c->n_edge > 0 ? 1 : 0) : launches_per_step(c);
+    c->part_done |= part;
+    if (c->part_done == (LBM_STEP_EDGE | LBM_STEP_INTERIOR)) {
+        c->part_done = 0;
         c->cur ^= 1;
         c->steps += 1;
     }
@@ -1536,29 +1578,38 @@ int lbm_set_open_x(lbm_ctx* c, int lat, const uint8_t* halo_mask) {
     return LBM_OK;
 }
 
-static int halo_call(lbm_ctx* c, int lat, int side, void* buf, bool pack) {
+static int halo_call(lbm_ctx* c, int lat, int side, void* buf, bool pack, void* stream) {
     int rc = check_lat(c, lat);
     if (rc) return rc;
     if (!geom_open_x(c->lats[lat].geom)) return fail(LBM_EINVAL, "lattice %d is not open in x (lbm_set_open_x)", lat);
     if (side != 0 && side != 1) return fail(LBM_EINVAL, "side=%d must be 0 (left) or 1 (right)", side);
     if (!buf) return fail(LBM_EINVAL, "null halo buffer");
+    // during a split step, the buffer that step writes (its edge part must
+    // have run before a pack); else the state the next step reads
+    int b = c->cur;
+    if (c->part_done) {
+        if (pack && !(c->part_done & LBM_STEP_EDGE))
+            return fail(LBM_EINVAL, "halo pack during a split step needs its edge part first");
+        b = 1 - c->cur;
+    }
     const Geom& g = c->lats[lat].geom;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     cudaError_t e = c->precision == LBM_FP64
-                        ? launch_halo_f64(g, (double*)c->f[c->cur], side, (double*)buf, pack, c->stream)
-                        : launch_halo_f32(g, (float*)c->f[c->cur], side, (float*)buf, pack, c->stream);
+                        ? launch_halo_f64(g, (double*)c->f[b], side, (double*)buf, pack, s)
+                        : launch_halo_f32(g, (float*)c->f[b], side, (float*)buf, pack, s);
     if (e != cudaSuccess) return cuda_fail(e, pack ? "halo pack" : "halo unpack");
     c->launches += 1;
     return LBM_OK;
 }
 
-int lbm_halo_pack(lbm_ctx* c, int lat, int side, void* dev_out) {
+int lbm_halo_pack(lbm_ctx* c, int lat, int side, void* dev_out, void* cuda_stream) {
     Range range("lbm_halo_pack");
-    return halo_call(c, lat, side, dev_out, true);
+    return halo_call(c, lat, side, dev_out, true, cuda_stream);
 }
 
-int lbm_halo_unpack(lbm_ctx* c, int lat, int side, const void* dev_in) {
+int lbm_halo_unpack(lbm_ctx* c, int lat, int side, const void* dev_in, void* cuda_stream) {
     Range range("lbm_halo_unpack");
-    return halo_call(c, lat, side, const_cast<void*>(dev_in), false);
+    return halo_call(c, lat, side, const_cast<void*>(dev_in), false, cuda_stream);
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }

@@ -44,6 +44,7 @@ EXPORTED = [
     "lbm_tile_count", "lbm_tile_shape", "lbm_tile_kind", "lbm_set_tile", "lbm_autotune", "lbm_info",
     "lbm_last_error", "lbm_destroy", "lbm_total_mass_fp32_noalloc", "lbm_get_state_view",
     "lbm_set_open_x", "lbm_halo_pack", "lbm_halo_unpack", "lbm_total_momentum", "lbm_totals_all",
+    "lbm_step_part",
 ]
 
 
@@ -140,8 +141,9 @@ def load(build_if_missing: bool = True):
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_total_mass_fp32_noalloc.argtypes = [_vp, I, I, ctypes.c_double, _vp, _vp, _vp]
     lib.lbm_set_open_x.argtypes = [_ctx, I, _vp]
-    lib.lbm_halo_pack.argtypes = [_ctx, I, I, _vp]
-    lib.lbm_halo_unpack.argtypes = [_ctx, I, I, _vp]
+    lib.lbm_halo_pack.argtypes = [_ctx, I, I, _vp, _vp]
+    lib.lbm_halo_unpack.argtypes = [_ctx, I, I, _vp, _vp]
+    lib.lbm_step_part.argtypes = [_ctx, I]
     lib.lbm_destroy.argtypes = [_ctx]
     lib.lbm_destroy.restype = None
     for name in EXPORTED:
@@ -207,16 +209,24 @@ def lbm_set_open_x(ctx, lat, halo_mask=None):
     _check(load().lbm_set_open_x(ctx, lat, None if hm is None else hm.ctypes.data))
 
 
-def lbm_halo_pack(ctx, lat, side, dev_out_ptr):
-    _check(load().lbm_halo_pack(ctx, lat, int(side), ctypes.c_void_p(dev_out_ptr)))
+def lbm_halo_pack(ctx, lat, side, dev_out_ptr, stream_handle=0):
+    _check(load().lbm_halo_pack(ctx, lat, int(side), ctypes.c_void_p(dev_out_ptr), stream_handle or None))
 
 
-def lbm_halo_unpack(ctx, lat, side, dev_in_ptr):
-    _check(load().lbm_halo_unpack(ctx, lat, int(side), ctypes.c_void_p(dev_in_ptr)))
+def lbm_halo_unpack(ctx, lat, side, dev_in_ptr, stream_handle=0):
+    _check(load().lbm_halo_unpack(ctx, lat, int(side), ctypes.c_void_p(dev_in_ptr), stream_handle or None))
 
 
 def lbm_step(ctx, n):
     _check(load().lbm_step(ctx, int(n)))
+
+
+LBM_STEP_EDGE = 1       # lbm_step_part: the tiles within two cells of an open x edge
+LBM_STEP_INTERIOR = 2   # every other tile
+
+
+def lbm_step_part(ctx, part):
+    _check(load().lbm_step_part(ctx, int(part)))
 
 
 def lbm_read_moments(ctx, lat, rho=None, ux=None, uy=None, p=None, allow_flags=False):

@@ -10,6 +10,11 @@ common stream) or between ranks, one slab per rank in rank order along x
 (``RankSlab``, ``torch.distributed`` point-to-point: device buffers under
 NCCL, host copies under gloo). Every arithmetic step runs in the library's
 kernels.
+
+With ``overlap=True`` each step is split (``lbm_step_part``): the tiles
+next to the cuts first, then the halo is packed, exchanged and unpacked on a
+stream of its own while the rest of the step runs; the next step waits for
+the unpack. The result is bitwise the same.
 """
 from dataclasses import replace
 from typing import List, Optional, Sequence
@@ -58,43 +63,61 @@ class _Slab:
         self.out = [torch.empty(n, dtype=dtype, device="cuda") for _ in range(2)]   # packed for side 0, 1
         self.inc = [torch.empty(n, dtype=dtype, device="cuda") for _ in range(2)]   # received from side 0, 1
 
-    def pack(self):
+    def pack(self, stream=None):
+        h = stream.cuda_stream if stream is not None else 0
         for side in (0, 1):
-            lbm.lbm_halo_pack(self.batch.ctx, 0, side, self.out[side].data_ptr())
+            lbm.lbm_halo_pack(self.batch.ctx, 0, side, self.out[side].data_ptr(), h)
 
-    def unpack(self):
+    def unpack(self, stream=None):
+        h = stream.cuda_stream if stream is not None else 0
         for side in (0, 1):
-            lbm.lbm_halo_unpack(self.batch.ctx, 0, side, self.inc[side].data_ptr())
+            lbm.lbm_halo_unpack(self.batch.ctx, 0, side, self.inc[side].data_ptr(), h)
 
 
 class LocalSlabs:
     """The slabs of one lattice as contexts on the current device, stepped
     together; halos move by device copies on the contexts' common stream."""
 
-    def __init__(self, spec, cuts: Sequence[int], precision="fp32_dev", stream=None):
+    def __init__(self, spec, cuts: Sequence[int], precision="fp32_dev", stream=None, overlap=False):
         import torch
         self.spec = spec
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.overlap = overlap
+        self.comm = torch.cuda.Stream() if overlap else self.stream
         self.slabs = [_Slab(spec, a, b, precision, self.stream) for a, b in zip(cuts[:-1], cuts[1:])]
-        self.exchange()
+        self.exchange(self.stream)
 
-    def exchange(self):
+    def exchange(self, stream):
         import torch
         n = len(self.slabs)
-        with torch.cuda.stream(self.stream):
+        with torch.cuda.stream(stream):
             for s in self.slabs:
-                s.pack()
+                s.pack(stream)
             for k, s in enumerate(self.slabs):
                 s.inc[0].copy_(self.slabs[(k - 1) % n].out[1])   # the left neighbour's right side
                 s.inc[1].copy_(self.slabs[(k + 1) % n].out[0])   # the right neighbour's left side
             for s in self.slabs:
-                s.unpack()
+                s.unpack(stream)
 
     def step(self, n: int = 1):
+        import torch
         for _ in range(n):
+            if not self.overlap:
+                for s in self.slabs:
+                    s.batch.step(1)
+                self.exchange(self.stream)
+                continue
             for s in self.slabs:
-                s.batch.step(1)
-            self.exchange()
+                lbm.lbm_step_part(s.batch.ctx, lbm.LBM_STEP_EDGE)
+            edge_done = torch.cuda.Event()
+            edge_done.record(self.stream)
+            self.comm.wait_event(edge_done)
+            self.exchange(self.comm)                       # runs beside the interior tiles
+            for s in self.slabs:
+                lbm.lbm_step_part(s.batch.ctx, lbm.LBM_STEP_INTERIOR)
+            unpacked = torch.cuda.Event()
+            unpacked.record(self.comm)
+            self.stream.wait_event(unpacked)               # the next step reads the frames
 
     def moments(self, allow_flags=False):
         """(rho, ux, uy, p) of the whole lattice, (ny, nx) each."""
@@ -114,26 +137,35 @@ class RankSlab:
     an order that pairs them correctly also when both neighbours are the same
     rank (two ranks)."""
 
-    def __init__(self, spec, precision="fp32_dev", cuts: Optional[Sequence[int]] = None, stream=None):
+    def __init__(self, spec, precision="fp32_dev", cuts: Optional[Sequence[int]] = None, stream=None,
+                 overlap=False):
         import torch
         import torch.distributed as dist
         self.rank, self.world = dist.get_rank(), dist.get_world_size()
         cuts = list(cuts) if cuts is not None else even_cuts(spec.nx, self.world)
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.overlap = overlap
+        self.comm = torch.cuda.Stream() if overlap else self.stream
         self.slab = _Slab(spec, cuts[self.rank], cuts[self.rank + 1], precision, self.stream)
         self.host = dist.get_backend() != "nccl"
-        self.exchange()
+        self.exchange(self.stream)
 
-    def exchange(self):
+    def exchange(self, stream, before_wait=None):
+        """Pack, send and receive, unpack, all on `stream`; `before_wait`
+        (if given) is called once the sends and receives are posted, before
+        anything waits for them."""
         import torch
         import torch.distributed as dist
         s = self.slab
         left, right = (self.rank - 1) % self.world, (self.rank + 1) % self.world
-        # everything on the slab's stream: under NCCL the sends read the
-        # packed buffers after the pack, and wait() orders the unpack after
-        # the receives; under gloo the copies to the host synchronise it
-        with torch.cuda.stream(self.stream):
-            s.pack()
+        # everything on `stream`: under NCCL the sends read the packed
+        # buffers after the pack, and wait() orders the unpack after the
+        # receives; under gloo the copies to the host synchronise it
+        with torch.cuda.stream(stream):
+            s.pack(stream)
+            if before_wait is not None and self.host:
+                before_wait()    # the copies to the host below block this thread
+                before_wait = None
             if self.host:
                 out = [t.cpu() for t in s.out]
                 inc = [torch.empty_like(t) for t in out]
@@ -141,17 +173,34 @@ class RankSlab:
                 out, inc = s.out, s.inc
             ops = [dist.P2POp(dist.isend, out[1], right, tag=1), dist.P2POp(dist.irecv, inc[0], left, tag=1),
                    dist.P2POp(dist.isend, out[0], left, tag=0), dist.P2POp(dist.irecv, inc[1], right, tag=0)]
-            for r in dist.batch_isend_irecv(ops):
+            reqs = dist.batch_isend_irecv(ops)
+            if before_wait is not None:
+                before_wait()
+            for r in reqs:
                 r.wait()
             if self.host:
                 s.inc[0].copy_(inc[0])
                 s.inc[1].copy_(inc[1])
-            s.unpack()
+            s.unpack(stream)
 
     def step(self, n: int = 1):
+        import torch
+        ctx = self.slab.batch.ctx
         for _ in range(n):
-            self.slab.batch.step(1)
-            self.exchange()
+            if not self.overlap:
+                self.slab.batch.step(1)
+                self.exchange(self.stream)
+                continue
+            lbm.lbm_step_part(ctx, lbm.LBM_STEP_EDGE)
+            edge_done = torch.cuda.Event()
+            edge_done.record(self.stream)
+            self.comm.wait_event(edge_done)
+            # the interior tiles are launched before anything waits for the
+            # messages, so they run while the halo travels
+            self.exchange(self.comm, before_wait=lambda: lbm.lbm_step_part(ctx, lbm.LBM_STEP_INTERIOR))
+            unpacked = torch.cuda.Event()
+            unpacked.record(self.comm)
+            self.stream.wait_event(unpacked)
 
     def moments(self, allow_flags=False):
         return self.slab.batch.moments(0, allow_flags=allow_flags)

@@ -41,15 +41,17 @@ def _first_of(kind):
     return next(t for t in range(lbm.lbm_tile_count()) if lbm.lbm_tile_kind(t) == kind)
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("precision,kind", [("fp32_dev", lbm.LBM_TILE_PLAIN), ("fp32_dev", lbm.LBM_TILE_TMA),
                                             ("fp32_dev", lbm.LBM_TILE_PIPELINED), ("fp64", lbm.LBM_TILE_PLAIN)])
-def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind):
+def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind, overlap):
     """Every step-kernel kind on the slabs (the TMA and pipelined kernels take
     the slabs' interior tiles, the plain kernel's general path the tiles
-    along the cuts)."""
+    along the cuts); with overlap, each step split into the tiles along the
+    cuts and the rest, the exchange on a second stream beside the rest."""
     spec = _spec()
     ref, mass, mom = _whole(spec, precision, STEPS, momentum=True)
-    slabs = xslab.LocalSlabs(spec, [0, 37, 59, 96], precision)   # widths 37, 22, 37
+    slabs = xslab.LocalSlabs(spec, [0, 37, 59, 96], precision, overlap=overlap)   # widths 37, 22, 37
     tile = 1 if kind == lbm.LBM_TILE_PLAIN else _first_of(kind)
     for s in slabs.slabs:
         lbm.lbm_set_tile(s.batch.ctx, tile)
@@ -65,13 +67,15 @@ def test_slabs_in_one_process_equal_the_whole_lattice(precision, kind):
     slabs.close()
 
 
-def test_narrow_slabs_equal_the_whole_lattice():
+@pytest.mark.parametrize("overlap", [False, True])
+def test_narrow_slabs_equal_the_whole_lattice(overlap):
     """Five slabs, two of them at the minimum width of 2 columns and one of
     3: every node of those slabs is an edge node whose pulls and psi ring
-    reach into both neighbours' halos."""
+    reach into both neighbours' halos (with overlap their whole step is the
+    edge part)."""
     spec = _spec()
     ref, _ = _whole(spec, "fp32_dev", STEPS)
-    slabs = xslab.LocalSlabs(spec, [0, 2, 5, 40, 42, 96], "fp32_dev")
+    slabs = xslab.LocalSlabs(spec, [0, 2, 5, 40, 42, 96], "fp32_dev", overlap=overlap)
     slabs.step(STEPS)
     for name, a, b in zip(("rho", "ux", "uy", "p"), slabs.moments(), ref):
         assert np.array_equal(a, b), name
@@ -109,7 +113,53 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, q, steps):
+def test_split_step_equals_one_step():
+    """lbm_step_part on a batch with and without x-slabs: both orders of the
+    parts give lbm_step's result bit for bit; the rules of a split step."""
+    specs = [small_spec(70, 45, walls=True, seed=81), small_spec(33, 20, seed=82)]
+    ref = lbm.Batch(specs, "fp32_dev")
+    ref.init()
+    ref.step(6)
+    want = [ref.moments(i) for i in range(2)]
+    ref.close()
+    for order in ((lbm.LBM_STEP_EDGE, lbm.LBM_STEP_INTERIOR), (lbm.LBM_STEP_INTERIOR, lbm.LBM_STEP_EDGE)):
+        b = lbm.Batch(specs, "fp32_dev")
+        b.init()
+        for _ in range(6):
+            for part in order:
+                lbm.lbm_step_part(b.ctx, part)
+        assert b.info()["steps"] == 6
+        for i in range(2):
+            for x, y in zip(b.moments(i), want[i]):
+                assert np.array_equal(x, y)
+        lbm.lbm_step_part(b.ctx, lbm.LBM_STEP_EDGE)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step_part(b.ctx, lbm.LBM_STEP_EDGE)       # the same part twice
+        assert e.value.code == lbm.LBM_EINVAL
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_step(b.ctx, 1)                           # a split step is half done
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_step_part(b.ctx, 3)
+        lbm.lbm_step_part(b.ctx, lbm.LBM_STEP_INTERIOR)
+        lbm.lbm_step(b.ctx, 1)
+        b.close()
+    # a pack during a split step needs its edge part first
+    slab, rho_ext, halo = xslab.cut(_spec(), 0, 48)
+    b = lbm.Batch([slab], "fp32_dev")
+    lbm.lbm_set_open_x(b.ctx, 0, halo)
+    b.init([rho_ext])
+    torch = pytest.importorskip("torch")
+    buf = torch.empty(lbm.LBM_HALO_ROWS * slab.ny, dtype=torch.float32, device="cuda")
+    lbm.lbm_step_part(b.ctx, lbm.LBM_STEP_INTERIOR)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_halo_pack(b.ctx, 0, 0, buf.data_ptr())
+    assert e.value.code == lbm.LBM_EINVAL
+    lbm.lbm_step_part(b.ctx, lbm.LBM_STEP_EDGE)
+    lbm.lbm_halo_pack(b.ctx, 0, 0, buf.data_ptr())
+    b.close()
+
+
+def _rank(rank, world, port, q, steps, overlap=False):
     import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -118,7 +168,7 @@ def _rank(rank, world, port, q, steps):
     torch.cuda.set_device(0)
     spec = _spec()
     cuts = [0, 41, 96]
-    mine = xslab.RankSlab(spec, "fp32_dev", cuts=cuts)
+    mine = xslab.RankSlab(spec, "fp32_dev", cuts=cuts, overlap=overlap)
     mine.step(steps)
     # each rank's columns in a whole-lattice array, zero elsewhere (equal
     # shapes for the gather; the sum over ranks is exact)
@@ -133,13 +183,14 @@ def _rank(rank, world, port, q, steps):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_on_one_gpu_equal_the_whole_lattice():
+@pytest.mark.parametrize("overlap", [False, True])
+def test_two_gloo_ranks_on_one_gpu_equal_the_whole_lattice(overlap):
     import torch.multiprocessing as mp
     world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q, STEPS)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, STEPS, overlap)) for r in range(world)]
     for p in procs:
         p.start()
     got = q.get(timeout=120)
