@@ -219,8 +219,10 @@ int lbm_step(lbm_ctx* ctx, int n);
  *   LBM_STEP_INTERIOR  every other tile.
  * The step is complete (the state advances, the step count grows) once both
  * parts are launched, in either order; the result is bitwise lbm_step(ctx, 1).
- * LBM_EINVAL for another part value, a part launched twice for one step, and
- * lbm_step while a split step is half done. */
+ * Between the two parts the read-outs see the state before the step. While
+ * a split step is half done, lbm_step, lbm_init_fields*, lbm_save_state,
+ * lbm_load_state, lbm_set_tile, lbm_autotune and lbm_set_open_x return
+ * LBM_EINVAL, as do another part value and a part launched twice. */
 #define LBM_STEP_EDGE 1
 #define LBM_STEP_INTERIOR 2
 int lbm_step_part(lbm_ctx* ctx, int part);

@@ -658,6 +658,13 @@ int ensure_graph(lbm_ctx* c, int src) {
     return LBM_OK;
 }
 
+// Calls that replace the state or the tile lists wait for a split step's
+// second part.
+int check_whole_step(lbm_ctx* c, const char* what) {
+    if (c->part_done) return fail(LBM_EINVAL, "%s: a split step (lbm_step_part) is half done", what);
+    return LBM_OK;
+}
+
 int check_lat(lbm_ctx* c, int lat) {
     if (!c) return fail(LBM_EINVAL, "null context");
     if (lat < 0 || lat >= c->n) return fail(LBM_EINVAL, "lattice index %d outside [0, %d)", lat, c->n);
@@ -1076,6 +1083,7 @@ int lbm_set_stream(lbm_ctx* c, void* stream) {
 int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, const double* uy) {
     Range range("lbm_init_fields");
     int rc = check_lat(c, lat);
+    if (!rc) rc = check_whole_step(c, "lbm_init_fields");
     if (rc) return rc;
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
     rc = geom_open_x(c->lats[lat].geom) ? init_open(c, lat, rho, ux, uy) : init_range(c, lat, 1, rho, ux, uy);
@@ -1087,6 +1095,7 @@ int lbm_init_fields(lbm_ctx* c, int lat, const double* rho, const double* ux, co
 int lbm_init_fields_all(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
     Range range("lbm_init_fields_all");
     if (!c) return fail(LBM_EINVAL, "null context");
+    if (check_whole_step(c, "lbm_init_fields_all")) return LBM_EINVAL;
     if (!rho) return fail(LBM_EINVAL, "rho must not be null");
     if (any_open_x(c))
         return fail(LBM_EINVAL, "a lattice of this context is open in x: initialise it with lbm_init_fields "
@@ -1321,6 +1330,7 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
     Range range("lbm_save_state");
     size_t need = 0;
     int rc = lbm_state_size(c, &need);
+    if (!rc) rc = check_whole_step(c, "lbm_save_state");
     if (rc) return rc;
     if (!buf || bytes < need) return fail(LBM_EINVAL, "state buffer needs %zu bytes, got %zu", need, bytes);
     char* p = (char*)buf;
@@ -1344,6 +1354,7 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     Range range("lbm_load_state");
     size_t need = 0;
     int rc = lbm_state_size(c, &need);
+    if (!rc) rc = check_whole_step(c, "lbm_load_state");
     if (rc) return rc;
     if (!buf || bytes < need) return fail(LBM_EINVAL, "state blob has %zu bytes, need %zu", bytes, need);
     const char* p = (const char*)buf;
@@ -1395,6 +1406,7 @@ int lbm_tile_kind(int index, int* kind) {
 
 int lbm_set_tile(lbm_ctx* c, int index) {
     if (!c) return fail(LBM_EINVAL, "null context");
+    if (check_whole_step(c, "lbm_set_tile")) return LBM_EINVAL;
     if (index < 0 || index >= total_tiles())
         return fail(LBM_EINVAL, "tile index %d outside [0, %d)", index, total_tiles());
     if (index == c->tile_index) return LBM_OK;
@@ -1415,6 +1427,7 @@ int lbm_autotune(lbm_ctx* c, int steps, int* best_index, double* ms) {
     Range range("lbm_autotune");
     if (!c) return fail(LBM_EINVAL, "null context");
     if (steps < 1) return fail(LBM_EINVAL, "steps=%d must be >= 1", steps);
+    if (check_whole_step(c, "lbm_autotune")) return LBM_EINVAL;
     const size_t fbytes = (size_t)c->total_elems * c->elem;
     void* saved = nullptr;
     int rc = dev_alloc(c, &saved, fbytes);
@@ -1539,6 +1552,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
 int lbm_set_open_x(lbm_ctx* c, int lat, const uint8_t* halo_mask) {
     Range range("lbm_set_open_x");
     int rc = check_lat(c, lat);
+    if (!rc) rc = check_whole_step(c, "lbm_set_open_x");
     if (rc) return rc;
     HostLattice& L = c->lats[lat];
     Geom& g = L.geom;

@@ -140,6 +140,11 @@ def test_split_step_equals_one_step():
             lbm.lbm_step(b.ctx, 1)                           # a split step is half done
         with pytest.raises(lbm.LbmError):
             lbm.lbm_step_part(b.ctx, 3)
+        for call in (lambda: lbm.lbm_set_tile(b.ctx, 1), lambda: lbm.lbm_save_state(b.ctx),
+                     lambda: lbm.lbm_autotune(b.ctx, 1), lambda: b.init()):
+            with pytest.raises(lbm.LbmError) as e:
+                call()                                       # state and tiles wait for the second part
+            assert e.value.code == lbm.LBM_EINVAL
         lbm.lbm_step_part(b.ctx, lbm.LBM_STEP_INTERIOR)
         lbm.lbm_step(b.ctx, 1)
         b.close()
