@@ -24,7 +24,9 @@ def mixed_batch():
             obstacle_spec(),                                    # solid cells across the periodic edges
             small_spec(5, 3, seed=53),                          # smaller than a tile
             small_spec(1, 9, seed=54),                          # one column: its own x neighbours
-            spec_for("vdw", 40, 24, seed=55), spec_for("psi_exp1", 40, 24, seed=56)]
+            # every kind of psi: van der Waals, Eq. 12 (eps = 1/3), Peng-Robinson, Eq. 12 (eps = 0)
+            spec_for("vdw", 40, 24, seed=55), spec_for("psi_exp1", 40, 24, seed=56),
+            spec_for("pr", 40, 24, seed=57), spec_for("psi_exp0", 40, 24, seed=58)]
 
 
 def run(specs, precision, steps, tile=None, stream=None):
