@@ -145,6 +145,7 @@ struct lbm_ctx {
     // memory that the kernel writes through its mapped address (m_bad); a
     // flag equal to bad_gen was set by the current init call
     unsigned* h_bad = nullptr;
+    unsigned* h_status = nullptr;  // page-locked copy of d_status (read_status)
     unsigned* m_bad = nullptr;
     unsigned bad_gen = 0;
     std::vector<Phys<double>> phys_d;
@@ -288,6 +289,7 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->d_io);
     cudaFree(c->d_psi);
     cudaFreeHost(c->h_bad);
+    cudaFreeHost(c->h_status);
     delete c;
 }
 
@@ -679,10 +681,13 @@ int status_code(unsigned flags) {
     return LBM_OK;
 }
 
+// The status words after everything enqueued so far: one copy into
+// page-locked memory and one synchronisation, which also completes the
+// caller's own copies enqueued before (the read-outs rely on it).
 int read_status(lbm_ctx* c, std::vector<unsigned>& out) {
-    out.assign(c->n, 0u);
-    CK(cudaMemcpyAsync(out.data(), c->d_status, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_status, c->d_status, c->n * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    out.assign(c->h_status, c->h_status + c->n);
     return LBM_OK;
 }
 
@@ -852,6 +857,7 @@ int init_open(lbm_ctx* c, int lat, const double* rho, const double* ux, const do
 // lattice lat0's first node: per group of lattices that fits the staging
 // buffers, one or two kernel launches and one download per field (density
 // alone into a page-locked, mapped host buffer: one launch, no staging).
+// Enqueued only: the caller synchronises before it returns the arrays.
 int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, double* uy, double* p) {
     const long long S = c->stage_nodes;
     const long long base = c->lats[lat0].geom.node_off;
@@ -865,7 +871,6 @@ int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, doub
                                      : launch_density_f32(ls, (const float*)c->f[c->cur], out, c->stream);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_fail(e, "moments kernels");
-        CK(cudaStreamSynchronize(c->stream));
         return LBM_OK;
     }
     double* h[4] = {rho, ux, uy, p};
@@ -892,8 +897,7 @@ int moments_range(lbm_ctx* c, int lat0, int n_lat, double* rho, double* ux, doub
             if (h[k]) CK(cudaMemcpyAsync(h[k] + (gb - base), c->d_io + k * S, bytes, cudaMemcpyDeviceToHost, c->stream));
         a = b;
     }
-    CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return LBM_OK;  // the caller synchronises (read_status)
 }
 
 int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** out) {
@@ -1002,6 +1006,11 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     const size_t psi_bytes = std::max((size_t)c->stage_cells * sizeof(double),
                                       c->inplace ? (size_t)total_cells * c->elem : (size_t)0);
     if (!rc) rc = dev_alloc(c, &c->d_psi, psi_bytes);
+    if (!rc && cudaHostAlloc((void**)&c->h_status, n * sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_status = nullptr;
+        rc = fail(LBM_ENOMEM, "cudaHostAlloc(%zu bytes) failed", n * sizeof(unsigned));
+    }
     if (!rc && cudaHostAlloc((void**)&c->h_bad, n * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         c->h_bad = nullptr;

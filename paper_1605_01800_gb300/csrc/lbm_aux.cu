@@ -34,6 +34,78 @@ __device__ __forceinline__ double feq(int a, double rho, double ux, double uy) {
 // flags need no clearing and no copy back. In-place storage: the swapped
 // layout keeps the same values in the opposite planes; the natural layout
 // holds f_eq of the node itself in its own planes.
+// Density-only init (u = 0) of two-buffer storage and the swapped layout,
+// one CTA per 32 x 8 tile. Each stored value is w_b (rho - rho_ref) of the
+// node it streams into, and w takes three values (4/9, 1/9, 1/36), so the
+// tile and its one-cell frame get their deviation and its three products
+// once per cell, in FP64, rounded to the storage type, in shared memory; a
+// node's nine values are read from there. The operations are those of
+// init_kernel (the FP64 difference, the FP64 product, one rounding), so the
+// result is bitwise the same at a third of the FP64 operations.
+constexpr int kInitTX = 32, kInitTY = 8;
+__device__ __forceinline__ int weight_class(int b) { return b == 0 ? 0 : (b < 5 ? 1 : 2); }
+template <typename T>
+__global__ void __launch_bounds__(kInitTX * kInitTY, 4)
+    init_rho_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys, int lat0,
+                    const double* __restrict__ rho, const uint8_t* __restrict__ mask_base, T* __restrict__ f_base,
+                    unsigned* __restrict__ bad, unsigned gen, int layout) {
+    __shared__ T wd[3][kInitTY + 2][kInitTX + 2];  // (T)(w * (rho - rho_ref)) for w = 4/9, 1/9, 1/36
+    const int lat = lat0 + blockIdx.y;
+    const Geom g = geoms[lat];
+    const double rho_ref = phys[lat].rho_ref;
+    const uint8_t* mask = geom_mask(g) ? mask_base + g.mask_off : nullptr;
+    T* f = f_base + g.f_off;
+    rho += g.node_off;
+    const int tiles_x = (g.nx + kInitTX - 1) / kInitTX;
+    const int tiles = tiles_x * ((g.ny + kInitTY - 1) / kInitTY);
+    const int tid = threadIdx.y * kInitTX + threadIdx.x;
+    unsigned invalid = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {  // uniform over the CTA
+        const int x0 = (t % tiles_x) * kInitTX, y0 = (t / tiles_x) * kInitTY;
+        for (int k = tid; k < (kInitTX + 2) * (kInitTY + 2); k += kInitTX * kInitTY) {
+            const int cy = k / (kInitTX + 2), cx = k - cy * (kInitTX + 2);
+            // periodic images (a full modulo: a lattice may be narrower or
+            // lower than the tile); a cell past the lattice's end is only
+            // read by the nodes it neighbours periodically
+            const int x = wrap_index(x0 - 1 + cx, g.nx), y = wrap_index(y0 - 1 + cy, g.ny);
+            const double dd = rho[y * g.nx + x] - rho_ref;
+            wd[0][cy][cx] = (T)(kWeq[0] * dd);
+            wd[1][cy][cx] = (T)(kWeq[1] * dd);
+            wd[2][cy][cx] = (T)(kWeq[5] * dd);
+        }
+        __syncthreads();
+        const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+        if (x < g.nx && y < g.ny) {
+            T out[9];
+            if (is_solid(mask, g, x, y)) {
+                for (int b = 0; b < 9; ++b) out[b] = T(0);
+            } else {
+                const double r = rho[y * g.nx + x];
+                if (!(isfinite(r) && r > 0.0)) invalid = 1;
+#pragma unroll
+                for (int b = 0; b < 9; ++b) {
+                    int xt = x + kEx[b], yt = y + kEy[b];
+                    xt = xt < 0 ? xt + g.nx : (xt >= g.nx ? xt - g.nx : xt);
+                    yt = yt < 0 ? yt + g.ny : (yt >= g.ny ? yt - g.ny : yt);
+                    // a reflected link stores the node's own value, with the
+                    // weight of the same class
+                    const bool back = is_solid(mask, g, xt, yt);
+                    const int sy = back ? threadIdx.y + 1 : threadIdx.y + 1 + kEy[b];
+                    const int sx = back ? threadIdx.x + 1 : threadIdx.x + 1 + kEx[b];
+                    const T v = wd[weight_class(b)][sy][sx];
+                    if (layout == kLayoutSwapped)  // compile-time indices: out stays in registers
+                        out[opp(b)] = v;
+                    else
+                        out[b] = v;
+                }
+            }
+            store_node<T>(f, g, x, y, out);
+        }
+        __syncthreads();
+    }
+    if (invalid) bad[lat] = gen;
+}
+
 template <typename T>
 __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* __restrict__ phys,
                             int lat0, const double* __restrict__ rho, const double* __restrict__ ux,
@@ -47,11 +119,10 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
     rho += g.node_off;
     if (ux) ux += g.node_off;
     if (uy) uy += g.node_off;
-    const long long n = (long long)g.nx * g.ny;
+    const int n = g.nx * g.ny;  // < 2^31: 9 stored planes hold fewer than 2^31 elements
     unsigned invalid = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / g.nx, x = i - y * g.nx;
         T out[9];
         if (is_solid(mask, g, x, y)) {
             for (int b = 0; b < 9; ++b) out[b] = T(0);
@@ -61,12 +132,14 @@ __global__ void init_kernel(const Geom* __restrict__ geoms, const Phys<double>* 
         if (!(isfinite(rho[i]) && rho[i] > 0.0)) invalid = 1;
         if ((ux && !isfinite(ux[i])) || (uy && !isfinite(uy[i]))) invalid = 1;
         for (int b = 0; b < 9; ++b) {
-            long long j = i;
+            int j = i;
             int bb = b;
             if (layout != kLayoutNatural) {
-                const int xt = wrap_index(x + kEx[b], g.nx), yt = wrap_index(y + kEy[b], g.ny);
+                int xt = x + kEx[b], yt = y + kEy[b];
+                xt = xt < 0 ? xt + g.nx : (xt >= g.nx ? xt - g.nx : xt);
+                yt = yt < 0 ? yt + g.ny : (yt >= g.ny ? yt - g.ny : yt);
                 const bool back = is_solid(mask, g, xt, yt);
-                j = back ? i : (long long)yt * g.nx + xt;
+                j = back ? i : yt * g.nx + xt;
                 bb = back ? kOpp[b] : b;
             }
             double v;
@@ -428,8 +501,15 @@ dim3 lattice_grid(long long max_nodes, int n_lat, int threads) {
 template <typename T>
 cudaError_t init_impl(const LaunchSet& L, const double* rho, const double* ux, const double* uy,
                       T* f, unsigned* bad, unsigned gen, cudaStream_t s) {
-    init_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(
-        L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad, gen, L.layout);
+    if (ux == nullptr && uy == nullptr && L.layout != kLayoutNatural) {
+        long long tiles = (L.max_nodes + kInitTX * kInitTY - 1) / (kInitTX * kInitTY) + L.max_extent / 8 + 1;
+        if (tiles > 4096) tiles = 4096;
+        init_rho_kernel<T><<<dim3((unsigned)tiles, L.n_lat), dim3(kInitTX, kInitTY), 0, s>>>(
+            L.geoms, L.phys, L.lat0, rho, L.mask, f, bad, gen, L.layout);
+    } else {
+        init_kernel<T><<<lattice_grid(L.max_nodes, L.n_lat, 256), 256, 0, s>>>(
+            L.geoms, L.phys, L.lat0, rho, ux, uy, L.mask, f, bad, gen, L.layout);
+    }
     return cudaGetLastError();
 }
 
