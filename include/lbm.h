@@ -146,6 +146,10 @@ typedef struct {
     int n_tiles;               /* CTAs of one step launch */
     int graph_chunk;           /* steps per CUDA-graph replay in lbm_step */
     int inplace;               /* 1 for in-place storage (LBM_INPLACE) */
+    int l2_prefetch;           /* 1 when the two distribution arrays exceed the
+                                  device's L2: the FP32 step kernel then
+                                  prefetches later tiles' populations into L2
+                                  (no effect on results) */
 } lbm_info_t;
 
 /* Where one lattice's current state lives on the device (lbm_state_view),

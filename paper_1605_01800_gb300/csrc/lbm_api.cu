@@ -95,6 +95,9 @@ struct lbm_ctx {
     // in-place storage: one distribution array (f[1] == f[0]); cur is the
     // layout of the state, 0 natural, 1 swapped (kLayoutNatural/Swapped)
     bool inplace = false;
+    // the two distribution arrays exceed L2, so every step streams from DRAM:
+    // the plain kernel then prefetches later tiles into L2 (StepArgs::ahead)
+    bool streams_dram = false;
     uint8_t* d_mask = nullptr;
     Geom* d_geom = nullptr;
     Phys<float>* d_phys_f = nullptr;
@@ -607,11 +610,11 @@ cudaError_t launch_one_step(lbm_ctx* c, int src, int part = kPartAll) {
     const bool open = any_open_x(c);
     if (c->precision == LBM_FP64) {
         StepArgs<double> a{c->d_tiles + first, c->d_geom, c->d_phys_d, (const double*)c->f[src],
-                           (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo + first};
+                           (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo + first, 0};
         return launch_step_f64(c->tile_index, count, a, c->stream, open);
     }
     StepArgs<float> a{c->d_tiles + first, c->d_geom, c->d_phys_f, (const float*)c->f[src], (float*)c->f[1 - src],
-                      c->d_mask, c->d_status, c->d_tgeo + first};
+                      c->d_mask, c->d_status, c->d_tgeo + first, c->streams_dram ? 1 : 0};
     int plain_shape = c->tile_index;
     if (is_pipe(c->tile_index)) {
         const int v = c->tile_index - pipe_first();
@@ -979,6 +982,11 @@ int create_common(int n, const lbm_lattice_desc* desc, int precision, lbm_ctx** 
     const size_t fbytes = (size_t)c->total_elems * c->elem;
     if (!rc) rc = dev_alloc(c, &c->f[0], fbytes);
     if (!rc && !c->inplace) rc = dev_alloc(c, &c->f[1], fbytes);
+    if (!rc) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
+            c->streams_dram = 2 * fbytes > (size_t)l2;
+    }
     if (!rc && c->inplace) c->f[1] = c->f[0];
     if (!rc && m_off > 0) rc = dev_alloc(c, &c->d_mask, (size_t)m_off);
     if (!rc) rc = dev_alloc(c, &c->d_geom, n * sizeof(Geom));
@@ -1555,6 +1563,7 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->n_tiles = c->n_tiles + c->n_fast + c->n_tma;
     info->graph_chunk = kGraphChunk;
     info->inplace = c->inplace ? 1 : 0;
+    info->l2_prefetch = c->streams_dram && !c->inplace && c->precision != LBM_FP64 ? 1 : 0;
     return LBM_OK;
 }
 

@@ -45,6 +45,64 @@ struct StepArgs {
     const uint8_t* mask;
     unsigned* status;
     const TileGeom* tg;  // per entry of `tiles`: the tile and its lattice's geometry
+    // L2 prefetch distance in CTAs (0: none). The callers of the launch
+    // functions pass 1 (prefetch) or 0; the launch functions set the distance.
+    int ahead;
+};
+
+// The prefetch leads the reads by about DRAM latency x bandwidth under load
+// (about 1 us x 6.7 TB/s on GB300), whatever the tile shape: the distance in
+// tiles that keeps that many bytes of later tiles' reads on their way.
+// Measured on four workloads larger than L2 with four tile shapes, the best
+// leads hold 5.5-7.5 MB; leads of 2.5-3.5 MB, or of 14 MB and more, were
+// 4-18% slower on the 4096^2 lattice.
+constexpr long long kPrefetchLeadBytes = 7ll << 20;
+inline int prefetch_lead_tiles(int tile_read_bytes) {
+    return (int)((kPrefetchLeadBytes + tile_read_bytes - 1) / tile_read_bytes);
+}
+
+// L2 prefetch of the tile that the CTA blockIdx.x + ahead takes (CTAs start
+// in about index order): DRAM streams its populations while this CTA and the
+// ones between compute, and that CTA finds them in L2. Only for workloads
+// larger than L2; where the step's data stays in L2 from one step to the next
+// the prefetches only add requests (measured 2-5% slower). The tile's rows of the nine planes are TX * sizeof(T) bytes
+// each; thread t takes the 128-byte lines t, t + NT, ... (at most PF of them).
+// Rows past the lattice's last one are left out. The addresses are computed
+// before the CTA's own pulls and the prefetches issued after them, so that
+// the own loads go out first.
+struct NoAhead {
+    __device__ __forceinline__ void issue() const {}
+};
+template <typename T, int TX, int TY, int NT>
+struct AheadLines {
+    static constexpr int kLinesPerRow = TX * (int)sizeof(T) / 128;
+    static constexpr int kLines = 9 * TY * kLinesPerRow;
+    static constexpr int PF = (kLines + NT - 1) / NT;
+    const char* p[PF];
+    __device__ __forceinline__ void plan(const StepArgs<T>& A) {
+        static_assert(TX * sizeof(T) % 128 == 0, "tile rows are whole lines");
+#pragma unroll
+        for (int k = 0; k < PF; ++k) p[k] = nullptr;
+        const int next = (int)blockIdx.x + A.ahead;
+        if (A.ahead <= 0 || next >= (int)gridDim.x) return;
+        const Tile t = A.tg[next].t;
+        const Geom g = A.tg[next].g;
+        const int tid = threadIdx.y * TX + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int line = tid + k * NT;
+            const int a = line / (TY * kLinesPerRow);
+            const int rem = line - a * (TY * kLinesPerRow);
+            const int r = rem / kLinesPerRow, part = rem - r * kLinesPerRow;
+            if (line < kLines && t.y0 + r < g.ny)
+                p[k] = (const char*)(A.fin + g.f_off + a * g.plane + node_index(g, t.x0, t.y0 + r)) + 128 * part;
+        }
+    }
+    __device__ __forceinline__ void issue() const {
+#pragma unroll
+        for (int k = 0; k < PF; ++k)
+            if (p[k] != nullptr) asm volatile("prefetch.global.L2 [%0];" ::"l"(p[k]));
+    }
 };
 
 // ---- FP32 node math shared by the plain-load and the TMA kernels: nodes are
@@ -277,9 +335,9 @@ __device__ __forceinline__ void halo_ring_cell(int h, int& cx, int& cy) {
     }
 }
 
-template <int TX, int TYT, int RY>
+template <int TX, int TYT, int RY, typename PF>
 __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Tile& tile, const Geom& g,
-                                              const Phys<float>& P, float* s_psi) {
+                                              const Phys<float>& P, float* s_psi, const PF& ahead) {
     static_assert(RY % 2 == 0, "the fast path pairs nodes");
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
@@ -314,6 +372,7 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
 #pragma unroll
         for (int p = 0; p < NP; ++p) pull_pair(fin, plane, pitch, c0 + 2 * p * pitch, f[p]);
     }
+    ahead.issue();
 
     // halo ring: psi only
     float ph[NHT];
@@ -364,9 +423,9 @@ __device__ __forceinline__ void f32_tile_fast(const StepArgs<float>& A, const Ti
 // OPEN: the batch may hold lattices open in x (x-slabs), whose pulls across
 // the x edges read the frame instead of wrapping; instantiated apart, so
 // that the kernels of ordinary batches compile as if slabs did not exist.
-template <typename T, int TX, int TYT, int RY, bool OPEN>
+template <typename T, int TX, int TYT, int RY, bool OPEN, typename PF>
 __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& tile, const Geom& g,
-                                             const Phys<T>& P, T* s_psi) {
+                                             const Phys<T>& P, T* s_psi, const PF& ahead) {
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
@@ -395,6 +454,7 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
         if (live[r])
             live[r] = !pull_node<T>(fin, mask, plane, OPEN ? nbr_geom(g, x, y) : nbr_of(nx, ny, pitch, x, y), f[r]);
     }
+    ahead.issue();
 
     // ---- halo ring: psi only (issued before the own nodes' arithmetic)
     T ph[(NH + NT - 1) / NT];
@@ -520,14 +580,23 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
     else
         Pp = A.phys + tile.lat;
     const Phys<T>& P = *Pp;
-    if constexpr (std::is_same<T, float>::value && RY % 2 == 0) {
-        if (tile.clear && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4 &&
-            P.eos == EOS_CS) {
-            f32_tile_fast<TX, TYT, RY>(A, tile, g, P, s_psi);
-            return;
+    auto run = [&](const auto& ahead) {
+        if constexpr (std::is_same<T, float>::value && RY % 2 == 0) {
+            if (tile.clear && tile.x0 + TX <= g.nx && tile.y0 + TY <= g.ny && g.nx >= 4 && g.ny >= 4 &&
+                P.eos == EOS_CS) {
+                f32_tile_fast<TX, TYT, RY>(A, tile, g, P, s_psi, ahead);
+                return;
+            }
         }
+        tile_general<T, TX, TYT, RY, OPEN>(A, tile, g, P, s_psi, ahead);
+    };
+    if constexpr (std::is_same<T, float>::value) {
+        AheadLines<T, TX, TY, TX * TYT> ahead;
+        ahead.plan(A);
+        run(ahead);
+    } else {
+        run(NoAhead{});  // FP64 storage is bound by the FP64 units, not by DRAM latency
     }
-    tile_general<T, TX, TYT, RY, OPEN>(A, tile, g, P, s_psi);
 }
 
 }  // namespace lbm

@@ -75,7 +75,8 @@ class lbm_info_t(ctypes.Structure):
                 ("nodes", ctypes.c_longlong), ("fluid_nodes", ctypes.c_longlong),
                 ("steps", ctypes.c_longlong), ("kernel_launches", ctypes.c_ulonglong),
                 ("device_bytes", ctypes.c_size_t), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("n_tiles", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("inplace", ctypes.c_int)]
+                ("n_tiles", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("inplace", ctypes.c_int),
+                ("l2_prefetch", ctypes.c_int)]
 
 
 class lbm_state_view(ctypes.Structure):
