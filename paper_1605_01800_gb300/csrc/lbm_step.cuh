@@ -63,7 +63,9 @@ inline int prefetch_lead_tiles(int tile_read_bytes) {
 
 // L2 prefetch of the tile that the CTA blockIdx.x + ahead takes (CTAs start
 // in about index order): DRAM streams its populations while this CTA and the
-// ones between compute, and that CTA finds them in L2. Only for workloads
+// ones between compute, and that CTA finds them in L2. The last `ahead` CTAs
+// prefetch the first tiles of the next step instead, so that its first wave
+// finds its data in L2 too. Only for workloads
 // larger than L2; where the step's data stays in L2 from one step to the next
 // the prefetches only add requests (measured 2-5% slower). The tile's rows of the nine planes are TX * sizeof(T) bytes
 // each; thread t takes the 128-byte lines t, t + NT, ... (at most PF of them).
@@ -83,8 +85,18 @@ struct AheadLines {
         static_assert(TX * sizeof(T) % 128 == 0, "tile rows are whole lines");
 #pragma unroll
         for (int k = 0; k < PF; ++k) p[k] = nullptr;
-        const int next = (int)blockIdx.x + A.ahead;
-        if (A.ahead <= 0 || next >= (int)gridDim.x) return;
+        int next = (int)blockIdx.x + A.ahead;
+        const T* base = A.fin;
+        if (A.ahead <= 0) return;
+        if (next >= (int)gridDim.x) {
+            // the last CTAs of the launch: the first tiles of the next step,
+            // which reads what this step writes (those tiles' rows were
+            // written by the first CTAs of this launch, long finished). A
+            // hint only: if no such step follows, nothing reads them.
+            next -= (int)gridDim.x;
+            base = A.fout;
+            if (next >= (int)gridDim.x) return;
+        }
         const Tile t = A.tg[next].t;
         const Geom g = A.tg[next].g;
         const int tid = threadIdx.y * TX + threadIdx.x;
@@ -95,7 +107,7 @@ struct AheadLines {
             const int rem = line - a * (TY * kLinesPerRow);
             const int r = rem / kLinesPerRow, part = rem - r * kLinesPerRow;
             if (line < kLines && t.y0 + r < g.ny)
-                p[k] = (const char*)(A.fin + g.f_off + a * g.plane + node_index(g, t.x0, t.y0 + r)) + 128 * part;
+                p[k] = (const char*)(base + g.f_off + a * g.plane + node_index(g, t.x0, t.y0 + r)) + 128 * part;
         }
     }
     __device__ __forceinline__ void issue() const {
