@@ -150,6 +150,11 @@ typedef struct {
                                   device's L2: the FP32 step kernel then
                                   prefetches later tiles' populations into L2
                                   (no effect on results) */
+    int tile_grid;             /* 1 when the plain kernel's tiles form a regular
+                                  grid (every lattice alike, no walls, whole
+                                  tiles), so that its shapes of four nodes per
+                                  thread find tiles by arithmetic instead of
+                                  loading their records (no effect on results) */
 } lbm_info_t;
 
 /* Where one lattice's current state lives on the device (lbm_state_view),

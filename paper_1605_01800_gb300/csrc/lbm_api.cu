@@ -116,6 +116,10 @@ struct lbm_ctx {
     int pipe_grid = 0;
     Tile* d_tma = nullptr;
     int n_tma = 0;
+    // the plain kernel's list as a regular grid (tiles_x > 0), so that its
+    // FP32 shapes of four nodes per thread find tiles without loading their
+    // records (tile_at)
+    TileGrid grid{};
     // TMA variants: tensor maps per variant (box shape) and source buffer,
     // encoded once and passed to every launch as kernel parameters.
     static constexpr int kMaxTma = 8;
@@ -364,6 +368,34 @@ int build_tma(lbm_ctx* c, int tile_index) {
     return LBM_OK;
 }
 
+// The plain kernel's list as a regular grid of tx x ty tiles, if it is one:
+// every lattice with the same size and layout, no wall mask, not open in x,
+// covered by whole tiles, lattices evenly spaced in the distribution arrays,
+// and the list equal to the grid's order entry by entry (lattice by lattice,
+// row by row). Otherwise tiles_x = 0.
+TileGrid regular_grid(const lbm_ctx* c, const std::vector<Tile>& tiles, int tx, int ty) {
+    TileGrid none{};
+    if (c->n < 1) return none;
+    const Geom& g0 = c->lats[0].geom;
+    if (g0.nx % tx != 0 || g0.ny % ty != 0 || g0.flags != 0) return none;
+    const long long stride = c->n > 1 ? c->lats[1].geom.f_off - g0.f_off : 0;
+    for (int l = 0; l < c->n; ++l) {
+        const Geom& g = c->lats[l].geom;
+        if (g.nx != g0.nx || g.ny != g0.ny || g.pitch != g0.pitch || g.plane != g0.plane || g.flags != 0 ||
+            g.f_off != g0.f_off + (long long)l * stride)
+            return none;
+    }
+    const int tiles_x = g0.nx / tx, per_lat = tiles_x * (g0.ny / ty);
+    if ((long long)per_lat * c->n != (long long)tiles.size()) return none;
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        const int lat = (int)(k / per_lat), r = (int)(k % per_lat);
+        const Tile& t = tiles[k];
+        if (t.lat != lat || t.x0 != (r % tiles_x) * tx || t.y0 != (r / tiles_x) * ty || t.clear != 1) return none;
+    }
+    TileGrid grid{tiles_x, per_lat, stride, g0};
+    return grid;
+}
+
 // Work-lists of one step: every tile of every lattice, lattices in creation
 // order, tiles row-major within a lattice (in the plain kernel's list, the
 // tiles of its general path come first). The pipelined variants take the
@@ -448,6 +480,7 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     const int n_edge = (int)std::count_if(tiles.begin(), tiles.end(), open_edge);
     std::vector<TileGeom> tgeo(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) tgeo[k] = TileGeom{c->lats[tiles[k].lat].geom, tiles[k]};
+    const TileGrid grid = regular_grid(c, tiles, tx, ty);
     Tile* d = nullptr;
     TileGeom* dg = nullptr;
     FastTile* df = nullptr;
@@ -519,6 +552,7 @@ int build_tiles(lbm_ctx* c, int tile_index) {
     c->pipe_grid = pipe ? (int)std::min<long long>(c->n_fast, (long long)per_sm * sms) : 0;
     c->d_tma = di;
     c->n_tma = (int)inner_tiles.size();
+    c->grid = grid;
     c->tile_index = tile_index;
     drop_graphs(c);
     if (is_tma(tile_index)) return build_tma(c, tile_index);
@@ -608,6 +642,8 @@ cudaError_t launch_one_step(lbm_ctx* c, int src, int part = kPartAll) {
     const int first = part == kPartInterior ? c->n_edge : 0;
     const int count = part == kPartEdge ? c->n_edge : (part == kPartInterior ? c->n_tiles - c->n_edge : c->n_tiles);
     const bool open = any_open_x(c);
+    // the launch takes the plain kernel's whole list, in order
+    const bool whole_list = first == 0 && count == c->n_tiles;
     if (c->precision == LBM_FP64) {
         StepArgs<double> a{c->d_tiles + first, c->d_geom, c->d_phys_d, (const double*)c->f[src],
                            (double*)c->f[1 - src], c->d_mask, c->d_status, c->d_tgeo + first, 0};
@@ -615,6 +651,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src, int part = kPartAll) {
     }
     StepArgs<float> a{c->d_tiles + first, c->d_geom, c->d_phys_f, (const float*)c->f[src], (float*)c->f[1 - src],
                       c->d_mask, c->d_status, c->d_tgeo + first, c->streams_dram ? 1 : 0};
+    const TileGrid grid = whole_list && c->tile_index < kTileCount ? c->grid : TileGrid{};
     int plain_shape = c->tile_index;
     if (is_pipe(c->tile_index)) {
         const int v = c->tile_index - pipe_first();
@@ -634,7 +671,7 @@ cudaError_t launch_one_step(lbm_ctx* c, int src, int part = kPartAll) {
             e = launch_step_tma(v, c->tma_grid[v], ta, *c->h_maps[v][src], *c->h_table, c->stream);
         }
     }
-    if (e == cudaSuccess && count > 0) e = launch_step_f32(plain_shape, count, a, c->h_table, c->stream, open);
+    if (e == cudaSuccess && count > 0) e = launch_step_f32(plain_shape, count, a, c->h_table, grid, c->stream, open);
     return e;
 }
 
@@ -1564,6 +1601,8 @@ int lbm_info(lbm_ctx* c, lbm_info_t* info) {
     info->graph_chunk = kGraphChunk;
     info->inplace = c->inplace ? 1 : 0;
     info->l2_prefetch = c->streams_dram && !c->inplace && c->precision != LBM_FP64 ? 1 : 0;
+    info->tile_grid =
+        c->grid.tiles_x > 0 && !c->inplace && c->precision != LBM_FP64 && c->tile_index < kTileCount ? 1 : 0;
     return LBM_OK;
 }
 

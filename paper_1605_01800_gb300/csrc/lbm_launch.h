@@ -23,6 +23,7 @@ template <typename T>
 struct StepArgs;
 template <typename T>
 struct PhysTable;
+struct TileGrid;
 
 // TMA-staged persistent FP32 variants (lbm_step_tma.cu); tile indices
 // kTileCount .. kTileCount + tma_variant_count() - 1 of the public tile list.
@@ -86,14 +87,18 @@ cudaError_t launch_step_pipe(int v, int grid, const PipeArgs& a, const PhysTable
 // most kParamLattices lattices), or null to read them from global memory.
 // open: the batch holds lattices open in x (x-slabs); their kernels are
 // instantiated apart from the ordinary ones.
+// grid: the tile list as a regular grid (TileGrid::tiles_x > 0), which the
+// shapes of four nodes per thread use to find tiles without their records;
+// tiles_x = 0 otherwise (always for open batches and partial lists).
 cudaError_t launch_step_f32_closed(int tile_index, int n_tiles, const StepArgs<float>& a,
-                                   const PhysTable<float>* table, cudaStream_t s);
+                                   const PhysTable<float>* table, const TileGrid& grid, cudaStream_t s);
 cudaError_t launch_step_f32_open(int tile_index, int n_tiles, const StepArgs<float>& a,
-                                 const PhysTable<float>* table, cudaStream_t s);
+                                 const PhysTable<float>* table, const TileGrid& grid, cudaStream_t s);
 inline cudaError_t launch_step_f32(int tile_index, int n_tiles, const StepArgs<float>& a,
-                                   const PhysTable<float>* table, cudaStream_t s, bool open = false) {
-    return open ? launch_step_f32_open(tile_index, n_tiles, a, table, s)
-                : launch_step_f32_closed(tile_index, n_tiles, a, table, s);
+                                   const PhysTable<float>* table, const TileGrid& grid, cudaStream_t s,
+                                   bool open = false) {
+    return open ? launch_step_f32_open(tile_index, n_tiles, a, table, grid, s)
+                : launch_step_f32_closed(tile_index, n_tiles, a, table, grid, s);
 }
 cudaError_t launch_step_f64(int tile_index, int n_tiles, const StepArgs<double>& a, cudaStream_t s,
                             bool open = false);

@@ -76,7 +76,7 @@ class lbm_info_t(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("kernel_launches", ctypes.c_ulonglong),
                 ("device_bytes", ctypes.c_size_t), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("n_tiles", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("inplace", ctypes.c_int),
-                ("l2_prefetch", ctypes.c_int)]
+                ("l2_prefetch", ctypes.c_int), ("tile_grid", ctypes.c_int)]
 
 
 class lbm_state_view(ctypes.Structure):

@@ -56,3 +56,32 @@ def test_prefetch_rule():
         b = lbm.Batch(lattices(), precision)
         assert b.info()["l2_prefetch"] == expect, precision
         b.close()
+
+
+def test_regular_tile_grid_changes_no_result():
+    """Lattices alike in size, without walls and covered by whole tiles form a
+    regular grid of tiles: the 32 x 16 shapes (four nodes per thread) then
+    find their own tile and the tile they prefetch by arithmetic instead of
+    loading records. Bit for bit the two-node shapes' result (which load
+    records), on an L2-resident batch and on a prefetching one, and the same
+    lattices with walls (no grid) agree with themselves across shapes."""
+    grid_tiles = [t for t in range(lbm.lbm_tile_count())
+                  if lbm.lbm_tile_kind(t) == lbm.LBM_TILE_PLAIN and lbm.lbm_tile_shape(t) == (32, 16)]
+    small = [small_spec(256, 64, seed=90 + i, shape="bubble" if i % 2 else "droplet", R=12.0 + i)
+             for i in range(4)]
+    big = [small_spec(1024, 1024, seed=95), small_spec(1024, 1024, seed=96, shape="bubble", R=150.0)]
+    for specs, steps in ((small, 37), (big, 9)):
+        ref, info, ref_tot = run(specs, 1, steps)
+        assert info["tile_grid"] == 1
+        for t in grid_tiles:
+            got, info_t, tot = run(specs, t, steps)
+            assert info_t["tile_grid"] == 1 and info_t["l2_prefetch"] == info["l2_prefetch"]
+            assert np.array_equal(tot, ref_tot), t
+            for i in range(len(specs)):
+                for name, a, c in zip(("rho", "ux", "uy", "p"), got[i], ref[i]):
+                    assert np.array_equal(a, c), (t, i, name)
+    # no grid: lattices of different sizes, or walls
+    _, info, _ = run([small_spec(256, 64, seed=97), small_spec(128, 64, seed=98)], 3, 2)
+    assert info["tile_grid"] == 0
+    _, info, _ = run([small_spec(256, 64, walls=True, seed=99)], 3, 2)
+    assert info["tile_grid"] == 0
