@@ -392,7 +392,9 @@ TileGrid regular_grid(const lbm_ctx* c, const std::vector<Tile>& tiles, int tx, 
         const Tile& t = tiles[k];
         if (t.lat != lat || t.x0 != (r % tiles_x) * tx || t.y0 != (r / tiles_x) * ty || t.clear != 1) return none;
     }
-    TileGrid grid{tiles_x, per_lat, stride, g0};
+    TileGrid grid{tiles_x, per_lat, stride, g0, 0, 0, 0, 0};
+    div_magic_of(per_lat, &grid.m_lat, &grid.s_lat);
+    div_magic_of(tiles_x, &grid.m_x, &grid.s_x);
     return grid;
 }
 

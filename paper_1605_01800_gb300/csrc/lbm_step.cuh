@@ -37,12 +37,31 @@ using TableOf = typename std::conditional<TABLE, PhysTable<T>, NoTable>::type;
 
 // A work-list that is a regular grid of tiles (see tile_at): tiles_x tiles
 // per row of a lattice, tiles_per_lat per lattice, lattice l's populations
-// at g0.f_off + l * lat_stride. tiles_x == 0: not a grid.
+// at g0.f_off + l * lat_stride. tiles_x == 0: not a grid. The divisions by
+// tiles_per_lat and tiles_x are a multiplication and a shift (div_magic).
 struct TileGrid {
     int tiles_x, tiles_per_lat;
     long long lat_stride;
     Geom g0;
+    unsigned long long m_lat, m_x;  // magic multipliers of tiles_per_lat and tiles_x
+    int s_lat, s_x;                 // their shifts
 };
+
+// Division by a constant d as a multiplication and a shift (Granlund and
+// Montgomery's method, "Division by invariant integers using
+// multiplication", 1994): with s = ceil(log2 d) and m = ceil(2^(32+s) / d),
+// floor(n / d) = (n m) >> (32 + s) for every 0 <= n < 2^31 (the error of m,
+// below 1/d per unit of 2^(32+s), adds less than 1/(2d) to n/d), and n m
+// stays below 2^64.
+inline void div_magic_of(int d, unsigned long long* m, int* s) {
+    int l = 0;
+    while ((1ll << l) < (long long)d) ++l;
+    *s = l;
+    *m = ((1ull << (32 + l)) + (unsigned long long)d - 1) / (unsigned long long)d;
+}
+__device__ __forceinline__ int div_magic(int n, unsigned long long m, int s) {
+    return (int)(((unsigned long long)(unsigned)n * m) >> (32 + s));
+}
 
 template <typename T>
 struct StepArgs {
@@ -69,9 +88,9 @@ struct StepArgs {
 template <typename T, int TX, int TY>
 __device__ __forceinline__ void tile_at(const StepArgs<T>& A, const TileGrid& G, int b, Tile& t, Geom& g) {
     if (G.tiles_x > 0) {
-        const int lat = b / G.tiles_per_lat;
+        const int lat = div_magic(b, G.m_lat, G.s_lat);
         const int r = b - lat * G.tiles_per_lat;
-        const int row = r / G.tiles_x;
+        const int row = div_magic(r, G.m_x, G.s_x);
         t = Tile{lat, (r - row * G.tiles_x) * TX, row * TY, 1};
         g = G.g0;
         g.f_off += (long long)lat * G.lat_stride;
