@@ -619,9 +619,11 @@ __device__ __forceinline__ void tile_general(const StepArgs<T>& A, const Tile& t
 // tile; full tiles of wall-free lattices take the FP32 fast path (an
 // x-slab's tiles along its cuts are never marked clear). OPEN: see
 // tile_general.
-template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE, bool OPEN = false>
+// GRIDARG: the regular tile grid as a trailing argument (only the shapes
+// that use it take one, so the others keep their argument layout).
+template <typename T, int TX, int TYT, int RY, int MINB, bool TABLE, bool OPEN = false, typename... GRIDARG>
 __global__ void __launch_bounds__(TX * TYT, MINB)
-    step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT, const TileGrid G) {
+    step_kernel(StepArgs<T> A, const __grid_constant__ TableOf<T, TABLE> PT, const GRIDARG... grid_arg) {
     constexpr int TY = TYT * RY;
     constexpr int SW = TX + 2;
     constexpr int SH = TY + 2;
@@ -637,6 +639,9 @@ __global__ void __launch_bounds__(TX * TYT, MINB)
     // shapes of four nodes per thread only: there it measured 6% faster on a
     // 4096^2 lattice, in the two-node shapes 4% slower (same-box A/B).
     constexpr bool GRID = std::is_same<T, float>::value && RY == 4;
+    static_assert(sizeof...(GRIDARG) == (GRID ? 1 : 0), "the grid shapes take a TileGrid, the others none");
+    TileGrid G{};
+    if constexpr (GRID) G = (grid_arg, ...);
     const bool on_grid = GRID && G.tiles_x > 0;
     // CTA b asks L2 for line b of the tile records, so that the CTAs of
     // later waves find theirs there instead of in DRAM

@@ -6,7 +6,7 @@ namespace lbm {
 
 template <int TX, int TYT, int RY, bool OPEN>
 static cudaError_t launch_tile(int n_tiles, const StepArgs<double>& a, cudaStream_t s) {
-    step_kernel<double, TX, TYT, RY, 1, false, OPEN><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, NoTable{0}, TileGrid{});
+    step_kernel<double, TX, TYT, RY, 1, false, OPEN><<<n_tiles, dim3(TX, TYT), 0, s>>>(a, NoTable{0});
     return cudaGetLastError();
 }
 
